@@ -1,0 +1,333 @@
+"""Benchmark: complex quad-double MGS least squares, m=320, n=256, a sequence of solves.
+
+One step = one least-squares solve (MGS on [A b] + back substitution) of one system, on
+the GPU, through the C ABI; the systems are distinct, pre-generated and resident in HBM
+(a path tracker solving its Newton systems one after another).  The K timed systems
+(5.3 MB each) are all distinct, so every step reads data that is not in L2 from the step
+before (total far above the 129 MB L2).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead (a bounded
+sample of the same workload, scaled by the algorithmic work).  Multi-GPU: replicas only
+(the solves of a path are sequential; independent systems shard with no collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1210_0800_gb300 import inputs  # noqa: E402
+
+METRIC = "systems/s and FP64-pipe % of peak, complex DD/QD MGS least squares"
+
+WORKLOADS = {
+    # name: (limbs, m, n, extreme)
+    "c1_qd_320x256": (4, 320, 256, False),
+    "c0_dd_32x32": (2, 32, 32, False),
+    "c2_dd_256x256_extreme": (2, 256, 256, True),
+    "dd_64": (2, 64, 64, False),
+    "dd_128": (2, 128, 128, False),
+    "dd_256": (2, 256, 256, False),
+    "dd_512": (2, 512, 512, False),
+    "qd_64": (4, 64, 64, False),
+    "qd_128": (4, 128, 128, False),
+    "qd_256": (4, 256, 256, False),
+    "qd_512": (4, 512, 512, False),
+}
+DEFAULT = "c1_qd_320x256"
+
+# FP64 pipe instructions of the kernels' primitives (static counts of csrc/ddqd.cuh):
+# complex conjugated multiply-accumulate, complex update y -= c x, |x|^2 accumulate,
+# complex / real division.
+COST = {
+    2: dict(mac=36, upd=42, norm=18, div=22),
+    4: dict(mac=280, upd=322, norm=140, div=608),
+}
+# FP64 peak: 152 SMs x 4 sub-partitions x 0.5 FP64 lanes/clk (one DFMA warp-instruction
+# per 64 cycles per sub-partition, measured) at the 2070 MHz maximum SM clock.
+SMS, FP64_LANES_PER_CLK_SM = 152, 2.0
+
+
+def fp64_ops(L: int, m: int, n: int) -> float:
+    """Algorithmic FP64 instructions (lane operations) of one solve."""
+    c = COST[L]
+    nc = n + 1
+    pairs = nc * (nc - 1) / 2  # (pivot k, column j > k) of the augmented matrix
+    bulk = pairs * m * (c["mac"] + c["upd"])
+    norms = nc * m * c["norm"]
+    qdiv = n * m * c["div"]
+    backsub = n * (n - 1) / 2 * c["upd"] + n * c["div"]
+    return bulk + norms + qdiv + backsub
+
+
+def peak_fp64_ops_per_s(sm_max_mhz: float) -> float:
+    return SMS * FP64_LANES_PER_CLK_SM * sm_max_mhz * 1e6
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(L, m, n, seconds_target=3.0):
+    """Time the CPU oracle on a bounded sample of the workload: one system with the same m
+    and limbs and fewer columns, chosen so one solve takes a few seconds; returns
+    (systems/s scaled to the full workload by the algorithmic work, description)."""
+    import oracle
+
+    o = oracle.get()
+    # calibrate on a tiny system, then size the sample
+    ns = 8
+    A, xt, b = inputs.system(m, ns, L, inputs.BASE_SEED + 99)
+    t0 = time.perf_counter()
+    o.ls_solve(A, b)
+    t_small = time.perf_counter() - t0
+    scale = lambda k: m * (k + 1) ** 2  # noqa: E731  (work of MGS on [A b])
+    ns2 = int(max(ns, min(n, (ns + 1) * math.sqrt(seconds_target / max(t_small, 1e-6) * 1.0) - 1)))
+    A, xt, b = inputs.system(m, ns2, L, inputs.BASE_SEED + 98)
+    t0 = time.perf_counter()
+    o.ls_solve(A, b)
+    dt = time.perf_counter() - t0
+    sys_per_s = (1.0 / dt) * (fp64_ops(L, m, ns2) / fp64_ops(L, m, n))
+    desc = ("oracle ls_solve of one %s system m=%d n=%d (sample of the m=%d n=%d workload), %.2f s, scaled by "
+            "the algorithmic FP64-operation ratio %.4f" % ("QD" if L == 4 else "DD", m, ns2, m, n, dt,
+                                                          fp64_ops(L, m, ns2) / fp64_ops(L, m, n)))
+    del scale
+    return sys_per_s, desc, dt
+
+
+def run_reference(args, L, m, n, rank, world):
+    if rank != 0:
+        return 0
+    vals, descs = [], []
+    for _ in range(args.warmup):
+        oracle_sample(L, m, n, args.ref_seconds)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, d, _ = oracle_sample(L, m, n, args.ref_seconds)
+        vals.append(v)
+        descs.append(d)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "parallelism": "single CPU core"},
+        "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": descs[-1]},
+        "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, L, m, n, extreme, rank, world):
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fn = mg.ls_solve_dd if L == 2 else mg.ls_solve_qd
+    K, W = args.steps, args.warmup
+    total = K + W
+    # distinct systems for every step (rank-dependent seeds: replicas solve different systems)
+    seeds = [inputs.system_seed(inputs.BASE_SEED + 1, rank * 100000 + i) for i in range(total)]
+    host = [inputs.system(m, n, L, s, extreme=extreme) for s in seeds]
+    As = [torch.from_numpy(h[0]).to(dev) for h in host]
+    bs = [torch.from_numpy(h[2]).to(dev) for h in host]
+    xs = [torch.empty((n, 2, L), dtype=torch.float64, device=dev) for _ in range(total)]
+    ws = torch.empty(mg.mgs_workspace_bytes(L, m, n, True), dtype=torch.uint8, device=dev)
+    st = torch.zeros(total, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for i in range(W):
+        fn(As[i], bs[i], x=xs[i], workspace=ws, status=st[i:i + 1])
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for i in range(K):
+        j = W + i
+        ev[i][0].record(stream)
+        fn(As[j], bs[j], x=xs[j], workspace=ws, status=st[j:j + 1])
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    per_solve_ms = [a.elapsed_time(b) for a, b in ev]
+    statuses = st.cpu().numpy().tolist()
+    bad = [s for s in statuses if s != 0]
+
+    # end to end: pinned host buffers -> device, solve, x -> host, every step
+    Ah = [torch.from_numpy(h[0]).pin_memory() for h in host[:min(total, 8)]]
+    bh = [torch.from_numpy(h[2]).pin_memory() for h in host[:min(total, 8)]]
+    xh = torch.empty((n, 2, L), dtype=torch.float64).pin_memory()
+    Ad = torch.empty_like(As[0])
+    bd = torch.empty_like(bs[0])
+    xd = torch.empty_like(xs[0])
+    Ke = max(3, min(K, 10))
+    for i in range(2):
+        Ad.copy_(Ah[i % len(Ah)], non_blocking=True)
+        bd.copy_(bh[i % len(bh)], non_blocking=True)
+        fn(Ad, bd, x=xd, workspace=ws, status=st[0:1])
+        xh.copy_(xd, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(Ke):
+        Ad.copy_(Ah[i % len(Ah)], non_blocking=True)
+        bd.copy_(bh[i % len(bh)], non_blocking=True)
+        fn(Ad, bd, x=xd, workspace=ws, status=st[0:1])
+        xh.copy_(xd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / Ke
+    h2d = As[0].numel() * 8 + bs[0].numel() * 8
+    d2h = xs[0].numel() * 8
+
+    # max over ranks
+    ms = ms_total
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return 0
+
+    value = world * K / (ms / 1000.0)
+    kernel_ms = statistics.mean(per_solve_ms)
+    ops = fp64_ops(L, m, n)
+    peaks = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = peak_fp64_ops_per_s(sm_max)
+    achieved_ops = ops / (kernel_ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "extreme": extreme,
+                   "systems_per_step": 1, "l2": "inputs larger than L2 (every step a distinct 5 MB+ system)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": world / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": K,
+        "roofline": {"bound": "alu", "achieved": 2 * achieved_ops / 1e12, "peak": 2 * peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                     "note": "FP64 pipe: algorithmic FP64 instructions of the kernel's primitives per solve "
+                             "(%.4g) / CUDA-event time per solve; each instruction counted as one FMA slot "
+                             "(2 flops) like the peak (152 SMs x 2 DFMA/clk x %.0f MHz)" % (ops, sm_max)},
+        "kernel_ms": kernel_ms,
+        "status_errors": len(bad),
+    }
+    if clk:
+        line["clocks"] = clk
+    if world == 1 and not args.no_cpu_baseline:
+        v, desc, dt = oracle_sample(L, m, n, args.ref_seconds * 4)
+        line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": desc}
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-seconds", type=float, default=2.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    L, m, n, extreme = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        return run_reference(args, L, m, n, rank, world)
+    return run_gpu(args, L, m, n, extreme, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,107 @@
+/*
+ * mgs_ddqd.h -- C ABI of the GB300 (sm_103a) complex double-double / quad-double
+ * modified Gram-Schmidt least-squares library.
+ *
+ * Method: Verschelde & Yoffe, "Orthogonalization on a General Purpose Graphics Processing
+ * Unit with Double Double and Quad Double Arithmetic".
+ *
+ * Number format.  A real number is L float64 limbs (L = 2: double-double, L = 4:
+ * quad-double) whose exact sum is its value, largest limb first.  A complex element is
+ * 2L consecutive doubles {re_0..re_{L-1}, im_0..im_{L-1}} (32 bytes for DD, 64 for QD).
+ * Matrices are column-major BY ELEMENT: element (i, j) of a matrix with leading
+ * dimension ld starts at base + (j * ld + i) * 2L doubles.  Vectors are contiguous.
+ *
+ * Memory.  Every pointer is a DEVICE pointer into memory the caller owns (for example
+ * a PyTorch float64 CUDA tensor) and must be 16-byte aligned.  The library allocates
+ * nothing: scratch memory is the caller's `workspace` of at least
+ * mgs_workspace_bytes(...) bytes, valid for the duration of the call on `stream`.
+ *
+ * Execution.  Calls are stream-ordered and asynchronous: they enqueue work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream) and return without synchronising.
+ * The return value reports only what the host can detect (bad arguments, a CUDA launch
+ * failure).  What is found while the solve runs is written to *dev_status (one int32 in
+ * device memory, reset to MGS_OK by the call): MGS_ERANK, MGS_ENONFINITE or
+ * MGS_ETIMEOUT.  The first error recorded wins.  Outputs are unspecified when the
+ * status is not MGS_OK.  No exception crosses the ABI.
+ *
+ * Concurrency.  One call occupies the whole GPU with a cooperative launch (one CTA per
+ * SM at most); calls on the same stream run one after another.  A workspace must not be
+ * shared by calls that may run at the same time.
+ */
+#ifndef MGS_DDQD_H
+#define MGS_DDQD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (host return values and the device status word). */
+#define MGS_OK 0         /* success */
+#define MGS_EINVAL 1     /* host: invalid argument (null or misaligned pointer, m < n, n < 1, ld < m, ...) */
+#define MGS_ERANK 2      /* device: some r_kk is zero or not finite -- the method does not pivot (Section 4) */
+#define MGS_ENONFINITE 3 /* device: an input limb is Inf or NaN */
+#define MGS_ETIMEOUT 4   /* device: a wait between CTAs ran out of time; the kernel returned early */
+#define MGS_ECUDA 5      /* host: a CUDA call failed; mgs_last_cuda_error() returns its cudaError_t */
+#define MGS_ENOSPACE 6   /* host: workspace too small, or the problem exceeds what one GPU solve holds */
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int mgs_version(void);
+
+/* Human-readable name of a status code. */
+const char* mgs_status_string(int code);
+
+/* cudaError_t of the last call that returned MGS_ECUDA on this host thread. */
+int mgs_last_cuda_error(void);
+
+/*
+ * Bytes of workspace a call needs on the current device.
+ *   limbs    2 (DD) or 4 (QD)
+ *   m, n     matrix size (m >= n >= 1)
+ *   with_rhs 1 for ls_solve_* (augmented [A b]), 0 for mgs_qr_*
+ * Returns 0 for unsupported arguments or sizes.
+ */
+size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs);
+
+/*
+ * QR decomposition A = Q R by modified Gram-Schmidt (Section 3, Figure 1): for
+ * k = 1..n, r_kk = sqrt(a_k^H a_k), q_k = a_k / r_kk, and for j > k
+ * r_kj = q_k^H a_j, a_j = a_j - r_kj q_k, with x^H y = sum_l conj(x_l) y_l.
+ *   A        in: m x n matrix (lda >= m); out: Q (Q^H Q = I), overwriting A (Figure 2)
+ *   R        out: n x n upper triangle (ldr >= n), diagonal real and positive; the
+ *            strictly lower triangle is not written
+ *   workspace, workspace_bytes   caller-owned device scratch (see mgs_workspace_bytes)
+ *   dev_status  device int32, reset then set as described above
+ *   stream   cudaStream_t
+ * Host returns: MGS_OK, MGS_EINVAL, MGS_ENOSPACE or MGS_ECUDA.
+ */
+int mgs_qr_dd(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,
+              int32_t* dev_status, void* stream);
+int mgs_qr_qd(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,
+              int32_t* dev_status, void* stream);
+
+/*
+ * Least squares: x minimising ||b - A x||_2 (Section 3): modified Gram-Schmidt on the
+ * augmented matrix [A b] = [Q q_{n+1}] [[R y], [0 z]] (Eq. 1), so y = Q^H b and
+ * ||b - A x||^2 = ||R x - y||^2 + z^2, followed by the back substitution R x = y of
+ * Section 6, Figure 3 (x_k = y_k / r_kk, then y_j -= r_jk x_k for j < k).
+ *   A    in: m x n (lda >= m); out: Q
+ *   b    in: m-vector; out: the residual b - A x (the reduced last column of Eq. 1)
+ *   x    out: n-vector
+ *   R    out (optional, may be NULL): n x n upper triangle, ldr >= n when R != NULL
+ *   z    out (optional, may be NULL): L doubles, the residual norm z of Eq. 1 (real)
+ *   other arguments as for mgs_qr_*.
+ * Host returns: MGS_OK, MGS_EINVAL, MGS_ENOSPACE or MGS_ECUDA.
+ */
+int ls_solve_dd(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n,
+                void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n,
+                void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGS_DDQD_H */

@@ -1,0 +1,17 @@
+"""GB300-native complex double-double / quad-double modified Gram-Schmidt least squares.
+
+The compute path is the CUDA library ``lib/libmgs_ddqd.so`` (C ABI in include/mgs_ddqd.h);
+this package only builds it, marshals tensors into it, and generates synthetic inputs.
+"""
+
+from ._binding import (  # noqa: F401
+    MGSError,
+    STATUS_NAMES,
+    library_path,
+    load,
+    ls_solve_dd,
+    ls_solve_qd,
+    mgs_qr_dd,
+    mgs_qr_qd,
+    mgs_workspace_bytes,
+)

@@ -1,0 +1,85 @@
+"""Build the CUDA library in-tree: paper_1210_0800_gb300/lib/libmgs_ddqd.so (sm_103a).
+
+Translation units compile in parallel with nvcc, then link into one shared library
+with the CUDA runtime linked statically.  No PyTorch extension machinery is involved:
+the library has a plain C ABI (include/mgs_ddqd.h).
+"""
+
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+LIBDIR = os.path.join(HERE, "lib")
+LIBRARY = os.path.join(LIBDIR, "libmgs_ddqd.so")
+HOST_LIBRARY = os.path.join(LIBDIR, "libddqd_host.so")
+SOURCES = ["api.cu", "mgs_dd.cu", "mgs_qd.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--fmad=false"]
+
+
+def nvcc() -> str:
+    path = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(path):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
+    return path
+
+
+def _stale(objs) -> bool:
+    if not os.path.exists(LIBRARY):
+        return True
+    t = os.path.getmtime(LIBRARY)
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    deps.append(os.path.join(HERE, "..", "include", "mgs_ddqd.h"))
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    os.makedirs(LIBDIR, exist_ok=True)
+    objdir = os.path.join(LIBDIR, "_obj")
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
+    if not force and not _stale(objs):
+        return LIBRARY
+    cc = nvcc()
+    procs = []
+    for src, obj in zip(SOURCES, objs):
+        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
+        if verbose and out:
+            sys.stdout.write(out.decode(errors="replace"))
+    tmp = LIBRARY + ".tmp"
+    link = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    subprocess.check_call(link)
+    os.replace(tmp, LIBRARY)
+    return LIBRARY
+
+
+def build_host(force: bool = False) -> str:
+    """Host build of the device arithmetic (csrc/ddqd.cuh as plain C++) for the CPU tests."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    src = os.path.join(CSRC, "ddqd_host.cpp")
+    deps = [src, os.path.join(CSRC, "ddqd.cuh")]
+    if not force and os.path.exists(HOST_LIBRARY) and all(
+            os.path.getmtime(d) <= os.path.getmtime(HOST_LIBRARY) for d in deps):
+        return HOST_LIBRARY
+    tmp = HOST_LIBRARY + ".tmp"
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-fPIC", "-shared",
+                           "-Wno-unknown-pragmas", "-o", tmp, src])
+    os.replace(tmp, HOST_LIBRARY)
+    return HOST_LIBRARY
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_host(force="--force" in sys.argv))

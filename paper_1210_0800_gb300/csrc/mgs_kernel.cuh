@@ -1,0 +1,630 @@
+// Persistent modified Gram-Schmidt least-squares kernel (complex DD / QD) for sm_103a.
+//
+// Method (Verschelde & Yoffe):
+//   Section 3, Figure 1 -- MGS: r_kk = ||a_k||, q_k = a_k / r_kk, r_kj = q_k^H a_j,
+//                           a_j -= r_kj q_k for j > k;
+//   Section 3, Eq. (1)  -- MGS on the augmented [A b]: the last column ends as the
+//                           residual b - A x, its norm is z, and r_{k,n+1} = y_k = (Q^H b)_k;
+//   Section 6, Figure 3 -- back substitution R x = y, column by column.
+//
+// GPU organisation (not the paper's per-step launches): one cooperative launch of
+// Br x Bc CTAs that stays resident for the whole solve.
+//   * CTA (p, c) owns rows [p h, p h + h) of the augmented columns j = c, c + Bc, ...
+//     (column-cyclic, so every CTA keeps work as the trailing matrix shrinks) and keeps
+//     that tile in shared memory from the first step to the last.
+//   * Step k needs the Gram row G_kj = a_k^H a_j (j >= k) of the current columns; every
+//     CTA writes its row-block partials, one grid barrier, every CTA reduces the Br
+//     partials of the columns it owns (and of the pivot norm G_kk, identically everywhere).
+//     The update is a_j -= (G_kj / G_kk) a_k, i.e. r_kj q_k with r_kj = G_kj / r_kk and
+//     q_k = a_k / r_kk, so the pivot's square root and division stay off the update path.
+//   * Look-ahead: the owners of column k+1 update it first and publish its rows through a
+//     per-(step, row-block) flag; the other CTAs update their own columns meanwhile, then
+//     read the new pivot and form the partials of step k+1.  One grid barrier per step.
+//   * Deferred normalisation: during the sweep only G_kk and c_kj = G_kj / G_kk are needed;
+//     the square roots r_kk, the columns q_k = a_k / r_kk and r_kj = c_kj r_kk are formed
+//     once at the end, in parallel over all columns, from the unnormalised columns each
+//     CTA still holds.  On the critical path of a step there is then one division.
+//   * An FP64 instruction costs 64 cycles of the sub-partition's FP64 unit, so the latency
+//     chains of a step (coefficients, the look-ahead column) split the real and imaginary
+//     parts over two lanes.
+//   * Every spin-wait gives up after a time limit, records a timeout status and lets the
+//     remaining barriers fall through, so a missing CTA can never hang the GPU.
+#pragma once
+
+#include <cstdint>
+
+#include "ddqd.cuh"
+
+namespace mgs {
+
+enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ERANK = 2, ST_ENONFINITE = 3, ST_ETIMEOUT = 4 };
+
+constexpr int kThreads = 128;
+
+struct Params {
+  double* A;  // m x n, column-major by element, leading dimension lda (elements); Q on exit
+  long long lda;
+  double* b;  // m elements (augmented column) or nullptr for a plain QR
+  double* R;  // n x n, leading dimension ldr (elements)
+  long long ldr;
+  double* x;  // n elements (solution) or nullptr
+  double* z;  // L doubles (residual norm) or nullptr
+  int m, n, nc, aug;
+  int Br, Bc, h;
+  unsigned* sync;  // [0] barrier arrivals, [1] abort flag
+  int* flags;      // nc * Br pivot-ready flags
+  double* P;       // partial Gram rows: 2 * Br * nc * ACC
+  double* V;       // published pivot rows: 2 * Br * h * 2L
+  double* Y;       // y = Q^H b (and the back-substitution right-hand side): nc * 2L
+  double* Gd;      // pivot norms G_kk = ||a_k||^2: nc * L
+  double* Rd;      // r_kk: nc * L
+  double* Ri;      // 1 / r_kk: nc * L
+  int* status;
+  double one, nzero;
+  long long timeout_ns;
+};
+
+// ------------------------------------------------------------------ memory-model helpers
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
+
+// Grid-wide barrier on a monotone arrival counter.  Returns after all CTAs arrived, or
+// after the abort flag is seen, or after the time limit (then it raises the abort flag).
+__device__ __forceinline__ void grid_barrier(const Params& pr, unsigned& epoch) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned target = epoch * gridDim.x;
+    __threadfence();
+    atomicAdd(&pr.sync[0], 1u);
+    if (!ld_acquire_u32(&pr.sync[1])) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&pr.sync[0]) < target) {
+        if (ld_acquire_u32(&pr.sync[1])) break;
+        if ((++spins & 255u) == 0 && (long long)(globaltimer() - t0) > pr.timeout_ns) {
+          set_status(pr.status, ST_ETIMEOUT);
+          atomicExch(&pr.sync[1], 1u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Wait until flags[i] != 0 (bounded).  Called by one thread.
+__device__ __forceinline__ void wait_flag(const Params& pr, const int* flag) {
+  if (ld_acquire_u32(&pr.sync[1])) return;
+  const unsigned long long t0 = globaltimer();
+  unsigned spins = 0;
+  while (ld_acquire_s32(flag) == 0) {
+    if ((++spins & 255u) == 0) {
+      if (ld_acquire_u32(&pr.sync[1])) return;
+      if ((long long)(globaltimer() - t0) > pr.timeout_ns) {
+        set_status(pr.status, ST_ETIMEOUT);
+        atomicExch(&pr.sync[1], 1u);
+        return;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ tile access
+// Shared-memory planes: element (slot s, row l) limb q at base[(s * E + q) * h + l].
+template <class Ar>
+__device__ __forceinline__ typename Ar::elem sm_load(const double* base, int h, int l) {
+  typename Ar::elem e;
+#pragma unroll
+  for (int q = 0; q < 2 * Ar::L; ++q) e.v[q] = base[q * h + l];
+  return e;
+}
+template <class Ar>
+__device__ __forceinline__ void sm_store(double* base, int h, int l, const typename Ar::elem& e) {
+#pragma unroll
+  for (int q = 0; q < 2 * Ar::L; ++q) base[q * h + l] = e.v[q];
+}
+// Only the limbs of one part (0 real, 1 imaginary); the other part reads as zero.  Lanes
+// that own different parts of one element then never touch each other's limbs.
+template <class Ar>
+__device__ __forceinline__ typename Ar::elem sm_load_part(const double* base, int h, int l, int part) {
+  typename Ar::elem e;
+#pragma unroll
+  for (int q = 0; q < 2 * Ar::L; ++q) e.v[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < Ar::L; ++q) e.v[part * Ar::L + q] = base[(part * Ar::L + q) * h + l];
+  return e;
+}
+// Global element: 2L consecutive doubles, 16-byte aligned.
+template <class Ar>
+__device__ __forceinline__ typename Ar::elem g_load(const double* p) {
+  typename Ar::elem e;
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < Ar::L; ++i) {
+    const double2 v = q[i];
+    e.v[2 * i] = v.x;
+    e.v[2 * i + 1] = v.y;
+  }
+  return e;
+}
+template <class Ar>
+__device__ __forceinline__ typename Ar::elem g_load_cg(const double* p) {
+  typename Ar::elem e;
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < Ar::L; ++i) {
+    const double2 v = __ldcg(q + i);
+    e.v[2 * i] = v.x;
+    e.v[2 * i + 1] = v.y;
+  }
+  return e;
+}
+template <class Ar>
+__device__ __forceinline__ void g_store(double* p, const typename Ar::elem& e) {
+  double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+  for (int i = 0; i < Ar::L; ++i) q[i] = make_double2(e.v[2 * i], e.v[2 * i + 1]);
+}
+template <class Ar>
+__device__ __forceinline__ void acc_store(double* p, const typename Ar::acc& a) {
+  static_assert(sizeof(typename Ar::acc) == Ar::ACC * sizeof(double), "acc layout");
+  const double* s = reinterpret_cast<const double*>(&a);
+#pragma unroll
+  for (int i = 0; i < Ar::ACC; ++i) p[i] = s[i];
+}
+template <class Ar>
+__device__ __forceinline__ typename Ar::acc acc_load_cg(const double* p) {
+  typename Ar::acc a;
+  double* s = reinterpret_cast<double*>(&a);
+#pragma unroll
+  for (int i = 0; i < Ar::ACC; ++i) s[i] = __ldcg(p + i);
+  return a;
+}
+template <class Ar>
+__device__ __forceinline__ typename Ar::acc acc_shfl_xor(const typename Ar::acc& a, int mask) {
+  typename Ar::acc r;
+  const double* s = reinterpret_cast<const double*>(&a);
+  double* d = reinterpret_cast<double*>(&r);
+#pragma unroll
+  for (int i = 0; i < Ar::ACC; ++i) d[i] = __shfl_xor_sync(0xffffffffu, s[i], mask);
+  return r;
+}
+
+__device__ __forceinline__ int pow2_floor(int v) { return v <= 1 ? 1 : 1 << (31 - __clz(v)); }
+__device__ __forceinline__ int pow2_ceil(int v) { return v <= 1 ? 1 : 1 << (32 - __clz(v - 1)); }
+
+// Shared-memory footprint (bytes) of one CTA.
+__host__ __device__ inline size_t smem_bytes(int L, int h, int w) {
+  const size_t E = 2 * (size_t)L;
+  return sizeof(double) * ((size_t)(w + 2) * E * h  // tile + two pivot buffers
+                           + (size_t)(w + 1) * E     // coefficients + pivot norm
+                           + 4 * E)                  // scalars
+         + 16 * sizeof(int);
+}
+
+// Back substitution block size (rows of R solved by one CTA between grid barriers).
+constexpr int kBS = 32;
+
+// ------------------------------------------------------------------ the kernel
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
+  constexpr int L = Ar::L, E = 2 * L, ACC = Ar::ACC;
+  using elem = typename Ar::elem;
+  using acc = typename Ar::acc;
+  using real = typename Ar::real;
+  const Fp f{pr.one, pr.nzero};
+  const int tid = threadIdx.x;
+  const int Bc = pr.Bc, Br = pr.Br, nc = pr.nc, h = pr.h;
+  const int p = blockIdx.x / Bc, c = blockIdx.x % Bc;
+  const int r0 = p * h;
+  const int hr = max(0, min(h, pr.m - r0));  // rows of this block that exist
+  const int w = (nc - c + Bc - 1) / Bc;      // columns owned (slots)
+  unsigned epoch = 0;
+
+  extern __shared__ __align__(16) double sm[];
+  double* tile = sm;                         // w * E * h
+  double* piv = tile + (size_t)w * E * h;    // 2 * E * h
+  double* coef = piv + (size_t)2 * E * h;    // w * E
+  double* gkk = coef + (size_t)w * E;        // E (pivot norm, as an element)
+  double* scal = gkk + E;                    // 4 * E scratch
+  int* iflag = reinterpret_cast<int*>(scal + 4 * E);
+
+  auto col_of = [&](int s) { return c + s * Bc; };
+  auto colptr = [&](int j, int i) -> double* {
+    return (j < pr.n) ? pr.A + ((size_t)j * pr.lda + i) * E : pr.b + (size_t)i * E;
+  };
+  auto ld_real = [&](const double* src) {
+    real r;
+    double* d = reinterpret_cast<double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) d[q] = __ldcg(src + q);
+    return r;
+  };
+  auto st_real = [&](double* dst, const real& r) {
+    const double* d = reinterpret_cast<const double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) dst[q] = d[q];
+  };
+
+  // ---------------------------------------------------------------- load the tile
+  if (tid == 0) iflag[0] = 0;
+  __syncthreads();
+  {
+    bool bad = false;
+    for (int idx = tid; idx < w * h; idx += kThreads) {
+      const int s = idx / h, l = idx % h;
+      elem e;
+      if (l < hr) {
+        e = g_load<Ar>(colptr(col_of(s), r0 + l));
+#pragma unroll
+        for (int q = 0; q < E; ++q) bad |= !finite64(e.v[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) e.v[q] = 0.0;
+      }
+      sm_store<Ar>(tile + (size_t)s * E * h, h, l, e);
+    }
+    if (bad) iflag[0] = 1;
+  }
+  // pivot 0 rows (column 0 is unmodified at the start)
+  for (int l = tid; l < h; l += kThreads) {
+    elem e;
+    if (l < hr) {
+      e = g_load<Ar>(colptr(0, r0 + l));
+    } else {
+#pragma unroll
+      for (int q = 0; q < E; ++q) e.v[q] = 0.0;
+    }
+    sm_store<Ar>(piv, h, l, e);
+  }
+  __syncthreads();
+  if (tid == 0 && iflag[0]) set_status(pr.status, ST_ENONFINITE);
+
+  // Partials of the Gram row of pivot `kp` (pivot rows in pivbuf) for own columns j >= kp,
+  // written to P[buf].  g lanes share one column; lanes stride over the rows.
+  auto partials = [&](int kp, const double* pivbuf, int buf) {
+    const int s0 = (kp - c + Bc - 1) / Bc;  // first slot with column >= kp
+    const int first = max(s0, 0);
+    const int nact = w - first;
+    if (nact <= 0) return;
+    int g = pow2_floor(kThreads / nact);
+    g = min(g, 32);
+    g = min(g, pow2_ceil(max(hr, 1)));
+    const int groups = kThreads / g;
+    const int gi = tid / g, gl = tid % g;
+    for (int base = 0; base < nact; base += groups) {
+      const int s = first + base + gi;
+      acc a;
+      Ar::zero(a);
+      const bool act = (base + gi) < nact;
+      if (act) {
+        const int j = col_of(s);
+        const double* ts = tile + (size_t)s * E * h;
+        if (j == kp) {
+          for (int l = gl; l < hr; l += g) Ar::mac_norm(f, a, sm_load<Ar>(ts, h, l));
+        } else {
+          for (int l = gl; l < hr; l += g) Ar::mac_conj(f, a, sm_load<Ar>(pivbuf, h, l), sm_load<Ar>(ts, h, l));
+        }
+      }
+      for (int off = 1; off < g; off <<= 1) {
+        const acc o = acc_shfl_xor<Ar>(a, off);
+        Ar::combine(f, a, o);
+      }
+      if (act && gl == 0) {
+        const int j = col_of(s);
+        acc_store<Ar>(pr.P + (((size_t)buf * Br + p) * nc + j) * ACC, a);
+      }
+    }
+  };
+
+  partials(0, piv, 0);
+  grid_barrier(pr, epoch);
+
+  // ---------------------------------------------------------------- the steps
+  for (int k = 0; k < nc; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    const double* pcur = piv + (size_t)cur * E * h;
+    double* pnxt = piv + (size_t)nxt * E * h;
+    const bool own_k = (k % Bc) == c;
+    const bool last = (k == nc - 1);
+    const bool own_k1 = !last && ((k + 1) % Bc) == c;
+    const int s0 = (k + 1 - c + Bc - 1) / Bc;  // first slot with column > k
+    const int first = max(s0, 0);
+    const int nact = w - first;                // own columns j > k
+
+    // (1) reduce the Br partials of the pivot norm and of the own columns j > k
+    {
+      const int BrP = pow2_ceil(Br);
+      const int nred = 1 + max(nact, 0);
+      const int jobs = nred * BrP;
+      for (int base = 0; base < jobs; base += kThreads) {
+        const int job = base + tid;
+        const int ci = job / BrP, pp = job % BrP;
+        acc a;
+        Ar::zero(a);
+        const bool act = job < jobs && pp < Br;
+        if (act) {
+          const int j = (ci == 0) ? k : col_of(first + ci - 1);
+          a = acc_load_cg<Ar>(pr.P + (((size_t)cur * Br + pp) * nc + j) * ACC);
+        }
+        for (int off = 1; off < BrP; off <<= 1) {
+          const acc o = acc_shfl_xor<Ar>(a, off);
+          Ar::combine(f, a, o);
+        }
+        if (job < jobs && pp == 0) {
+          const elem g = Ar::finalize(f, a);
+          double* dst = (ci == 0) ? gkk : coef + (size_t)(first + ci - 1) * E;
+#pragma unroll
+          for (int q = 0; q < E; ++q) dst[q] = g.v[q];
+        }
+      }
+    }
+    __syncthreads();
+
+    // pivot norm G_kk (identical in every CTA)
+    elem gk;
+#pragma unroll
+    for (int q = 0; q < E; ++q) gk.v[q] = gkk[q];
+    const real G = Ar::re(gk);
+    const bool okpiv = Ar::positive(G);
+    if (blockIdx.x == 0 && tid == 0) {
+      st_real(pr.Gd + (size_t)k * L, G);
+      if (!okpiv && !(last && pr.aug)) set_status(pr.status, ST_ERANK);
+    }
+
+    if (last && pr.aug) {
+      // the right-hand-side column: what is left of it is the residual b - A x
+      if (own_k) {
+        const int s = k / Bc;
+        const double* ts = tile + (size_t)s * E * h;
+        for (int l = tid; l < hr; l += kThreads) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
+      }
+      break;
+    }
+
+    // (2) coefficients c_kj = G_kj / G_kk of the own columns j > k, one lane per part
+    {
+      const double invG = Ar::inv_lead(G);
+      for (int t = tid; t < 2 * nact; t += kThreads) {
+        double* cs = coef + (size_t)(first + (t >> 1)) * E;
+        const int part = t & 1;
+        const elem g = sm_load_part<Ar>(cs, 1, 0, part);
+        elem cc = g;
+        if (okpiv) {
+          Ar::div_real_part(f, cc, g, G, invG, part);
+        } else {
+#pragma unroll
+          for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < L; ++q) cs[part * L + q] = cc.v[part * L + q];
+      }
+    }
+    __syncthreads();
+
+    // (3) look-ahead: update column k+1 first and publish its rows
+    if (own_k1) {
+      const int s1 = (k + 1) / Bc;
+      double* ts = tile + (size_t)s1 * E * h;
+      elem cc;
+#pragma unroll
+      for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s1 * E + q];
+      for (int t = tid; t < 2 * hr; t += kThreads) {
+        const int l = t >> 1, part = t & 1;
+        elem y = sm_load_part<Ar>(ts, h, l, part);
+        Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+          ts[(part * L + q) * h + l] = y.v[part * L + q];
+          pnxt[(part * L + q) * h + l] = y.v[part * L + q];
+        }
+      }
+      for (int l = hr + tid; l < h; l += kThreads) {  // padding rows stay zero
+#pragma unroll
+        for (int q = 0; q < E; ++q) pnxt[q * h + l] = 0.0;
+      }
+      __syncthreads();
+      double* vdst = pr.V + ((size_t)nxt * Br + p) * h * E;
+      for (int l = tid; l < h; l += kThreads) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release_s32(pr.flags + (size_t)(k + 1) * Br + p, 1);
+      }
+    }
+
+    // (4) update the other own columns j > k+1 (one lane per element part)
+    {
+      const int sb = own_k1 ? first + 1 : first;  // slot of column k+1 is `first` when owned
+      const int nb = w - sb;
+      if (nb > 0 && hr > 0) {
+        const int tot = nb * hr * 2;
+        for (int idx = tid; idx < tot; idx += kThreads) {
+          const int part = idx & 1, rest = idx >> 1;
+          const int s = sb + rest / hr, l = rest % hr;
+          double* ts = tile + (size_t)s * E * h;
+          elem cc;
+#pragma unroll
+          for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
+          elem y = sm_load_part<Ar>(ts, h, l, part);
+          Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
+#pragma unroll
+          for (int q = 0; q < L; ++q) ts[(part * L + q) * h + l] = y.v[part * L + q];
+        }
+      }
+    }
+
+    // (5) coefficients of row k go to R (row k) and Y (column b); scaled by r_kk at the end
+    if (p == 0) {
+      for (int t = tid; t < nact; t += kThreads) {
+        const int s = first + t, j = col_of(s);
+        elem cc;
+#pragma unroll
+        for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
+        if (j < pr.n)
+          g_store<Ar>(pr.R + ((size_t)j * pr.ldr + k) * E, cc);
+        else
+          g_store<Ar>(pr.Y + (size_t)k * E, cc);
+      }
+    }
+
+    if (last) break;  // plain QR: every column has been reduced
+
+    // (6) the new pivot rows for the CTAs that do not own column k+1
+    if (!own_k1) {
+      if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
+      __syncthreads();
+      const double* vsrc = pr.V + ((size_t)nxt * Br + p) * h * E;
+      for (int l = tid; l < h; l += kThreads) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+    }
+    __syncthreads();
+
+    // (7) partials of step k+1
+    partials(k + 1, pnxt, nxt);
+    grid_barrier(pr, epoch);
+  }
+  grid_barrier(pr, epoch);
+
+  // ---------------------------------------------------------------- normalisation
+  const int nthreads = gridDim.x * kThreads;
+  const int gtid = blockIdx.x * kThreads + tid;
+  // (E1) r_kk = sqrt(G_kk) and 1 / r_kk for every column, spread over all threads
+  for (int k = gtid; k < nc; k += nthreads) {
+    const real G = ld_real(pr.Gd + (size_t)k * L);
+    const real r = Ar::sqrt(f, G);
+    st_real(pr.Rd + (size_t)k * L, r);
+    if (Ar::positive(r)) st_real(pr.Ri + (size_t)k * L, Ar::inv_real(f, r));
+    if (pr.aug && k == nc - 1 && pr.z) st_real(pr.z, r);
+  }
+  grid_barrier(pr, epoch);
+  // (E2) q_j = a_j / r_jj for the own columns (the tile holds the unnormalised columns)
+  {
+    const int nq = pr.n;  // columns that are normalised
+    const int wq = (nq - c + Bc - 1) / Bc;
+    if (wq > 0 && hr > 0) {
+      const int tot = wq * hr * 2;
+      for (int idx = tid; idx < tot; idx += kThreads) {
+        const int part = idx & 1, rest = idx >> 1;
+        const int s = rest / hr, l = rest % hr, j = col_of(s);
+        const real r = ld_real(pr.Rd + (size_t)j * L);
+        if (!Ar::positive(r)) continue;
+        const elem a = sm_load<Ar>(tile + (size_t)s * E * h, h, l);
+        elem q = a;
+        Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
+#pragma unroll
+        for (int qq = 0; qq < L; ++qq) pr.A[((size_t)j * pr.lda + r0 + l) * E + part * L + qq] = q.v[part * L + qq];
+      }
+    }
+  }
+  // (E3) r_kj = c_kj r_kk for the own columns (rows k < j split over the row blocks),
+  //      y_k = c_kn r_kk, and the real diagonal r_jj
+  {
+    for (int s = 0; s < w; ++s) {
+      const int j = col_of(s);
+      const int tot = j * 2;  // (k, part) pairs with k < j
+      for (int idx = p * kThreads + tid; idx < tot; idx += Br * kThreads) {
+        const int k = idx >> 1, part = idx & 1;
+        double* dst = (j < pr.n) ? pr.R + ((size_t)j * pr.ldr + k) * E : pr.Y + (size_t)k * E;
+        elem cc;
+#pragma unroll
+        for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < L; ++q) cc.v[part * L + q] = __ldcg(dst + part * L + q);
+        elem r = cc;
+        Ar::mul_real_part(f, r, cc, ld_real(pr.Rd + (size_t)k * L), part);
+#pragma unroll
+        for (int q = 0; q < L; ++q) dst[part * L + q] = r.v[part * L + q];
+      }
+      if (p == 0 && tid == 0 && j < pr.n) g_store<Ar>(pr.R + ((size_t)j * pr.ldr + j) * E,
+                                                     Ar::from_real(ld_real(pr.Rd + (size_t)j * L)));
+    }
+  }
+
+  // ---------------------------------------------------------------- back substitution
+  if (!pr.aug || pr.x == nullptr) return;
+  grid_barrier(pr, epoch);
+  // Figure 3, column by column, in blocks of kBS rows: CTA 0 runs the chain of the
+  // diagonal block (x_k = y_k / r_kk as y_k * (1/r_kk); y_j -= r_jk x_k for the block's
+  // rows j < k); then every CTA applies the block's x to the rows above it.
+  const int n = pr.n;
+  for (int e = n; e > 0; e -= kBS) {
+    const int s = max(0, e - kBS);
+    if (blockIdx.x == 0) {
+      double* ys = sm;  // (e - s) * E, row k at (k - s) * E
+      for (int i = tid; i < e - s; i += kThreads) {
+        const elem v = g_load_cg<Ar>(pr.Y + (size_t)(s + i) * E);
+#pragma unroll
+        for (int q = 0; q < E; ++q) ys[(size_t)i * E + q] = v.v[q];
+      }
+      __syncthreads();
+      for (int k = e - 1; k >= s; --k) {
+        double* yk = ys + (size_t)(k - s) * E;
+        if (tid < 2) {
+          const elem y = sm_load_part<Ar>(yk, 1, 0, tid);
+          elem x = y;
+          Ar::mul_real_part(f, x, y, ld_real(pr.Ri + (size_t)k * L), tid);
+#pragma unroll
+          for (int q = 0; q < L; ++q) {
+            yk[tid * L + q] = x.v[tid * L + q];  // x_k replaces y_k
+            pr.x[(size_t)k * E + tid * L + q] = x.v[tid * L + q];
+          }
+        }
+        __syncthreads();
+        elem xk;
+#pragma unroll
+        for (int q = 0; q < E; ++q) xk.v[q] = yk[q];
+        for (int t = tid; t < 2 * (k - s); t += kThreads) {
+          const int j = s + (t >> 1), part = t & 1;
+          double* yj = ys + (size_t)(j - s) * E;
+          elem y = sm_load_part<Ar>(yj, 1, 0, part);
+          Ar::update_part(f, y, g_load_cg<Ar>(pr.R + ((size_t)k * pr.ldr + j) * E), xk, part);
+#pragma unroll
+          for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
+        }
+        __syncthreads();
+      }
+    }
+    if (s == 0) break;
+    grid_barrier(pr, epoch);
+    // rows j < s: y_j -= sum_{k in [s, e)} r_jk x_k, one (row, part) per lane
+    {
+      const int tot = s * 2;
+      for (int idx = gtid; idx < tot; idx += nthreads) {
+        const int j = idx >> 1, part = idx & 1;
+        elem y;
+#pragma unroll
+        for (int q = 0; q < E; ++q) y.v[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < L; ++q) y.v[part * L + q] = __ldcg(pr.Y + (size_t)j * E + part * L + q);
+        for (int k = e - 1; k >= s; --k)
+          Ar::update_part(f, y, g_load_cg<Ar>(pr.R + ((size_t)k * pr.ldr + j) * E),
+                          g_load_cg<Ar>(pr.x + (size_t)k * E), part);
+#pragma unroll
+        for (int q = 0; q < L; ++q) pr.Y[(size_t)j * E + part * L + q] = y.v[part * L + q];
+      }
+    }
+    grid_barrier(pr, epoch);
+  }
+}
+
+}  // namespace mgs
