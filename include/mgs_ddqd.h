@@ -100,6 +100,25 @@ int ls_solve_dd(double* A, int lda, double* b, double* x, double* R, int ldr, do
 int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n,
                 void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 
+/*
+ * ls_solve_dd without a caller workspace, for callers that cannot allocate device memory
+ * (a host whose device memory is all owned by another allocator, or an application that
+ * must not allocate after start-up).  The paper has no counterpart: it is a packaging of
+ * ls_solve_dd.  Arguments and results are those of ls_solve_dd minus the workspace.
+ *   Scratch: a fixed device array of MGS_NOALLOC_WORKSPACE_BYTES inside the library,
+ *   held by every GPU that loads the library until the process exits.  No allocation
+ *   routine is called.
+ *   Sizes whose workspace (mgs_workspace_bytes(2, m, n, 1)) exceeds the array are rejected
+ *   with MGS_ENOSPACE (about n <= 350 for m = n).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current); make it before any stream capture.
+ *   Every call shares the array: calls that may overlap on the GPU race and must not be
+ *   issued.  Each call clears what must start at zero itself.
+ */
+#define MGS_NOALLOC_WORKSPACE_BYTES (4u * 1024u * 1024u)
+int ls_solve_dd_noalloc(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n,
+                        int32_t* dev_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@ from ._binding import (  # noqa: F401
     library_path,
     load,
     ls_solve_dd,
+    ls_solve_dd_noalloc,
     ls_solve_qd,
     mgs_qr_dd,
     mgs_qr_qd,

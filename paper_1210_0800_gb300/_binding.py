@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
                 5: "MGS_ECUDA", 6: "MGS_ENOSPACE"}
 
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
-           "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd"]
+           "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc"]
 
 _lib = None
 
@@ -56,6 +56,8 @@ def load(path: str | None = None):
     for name in ("ls_solve_dd", "ls_solve_qd"):
         getattr(lib, name).restype = i
         getattr(lib, name).argtypes = ls_args
+    lib.ls_solve_dd_noalloc.restype = i
+    lib.ls_solve_dd_noalloc.argtypes = [dp, i, dp, dp, dp, i, dp, i, i, vp, vp]
     if path == _build.LIBRARY:
         _lib = lib
     return lib
@@ -148,6 +150,30 @@ def ls_solve_dd(A, b, x=None, R=None, z=None, workspace=None, status=None, strea
 def ls_solve_qd(A, b, x=None, R=None, z=None, workspace=None, status=None, stream=None):
     """Complex QD least squares (MGS on [A b], back substitution); A -> Q, b -> residual."""
     return _ls_solve(4, A, b, x, R, z, workspace, status, stream)
+
+
+def ls_solve_dd_noalloc(A, b, x=None, R=None, z=None, status=None, stream=None):
+    """ls_solve_dd with the library's built-in scratch array instead of a workspace, for
+    callers that cannot allocate device memory (the outputs x and status must still be
+    given, or are created here for convenience).  Calls that may overlap on the GPU race."""
+    import torch
+
+    n, m = A.shape[0], A.shape[1]
+    _check_tensor(A, 2, 4, "A")
+    _check_tensor(b, 2, 3, "b")
+    if x is None:
+        x = torch.empty((n, 2, 2), dtype=torch.float64, device=A.device)
+    _check_tensor(x, 2, 3, "x")
+    if R is not None:
+        _check_tensor(R, 2, 4, "R")
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=A.device)
+    rc = load().ls_solve_dd_noalloc(_ptr(A), m, _ptr(b), _ptr(x), _ptr(R), n, _ptr(z), m, n, _ptr(status),
+                                    _stream(stream))
+    if rc != MGS_OK:
+        extra = " (cudaError %d)" % load().mgs_last_cuda_error() if rc == MGS_ECUDA else ""
+        raise MGSError(rc, "ls_solve_dd_noalloc%s" % extra)
+    return x, status
 
 
 def mgs_qr_dd(A, R=None, workspace=None, status=None, stream=None):

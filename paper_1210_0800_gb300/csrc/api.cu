@@ -147,6 +147,12 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
 
 }  // namespace
 
+namespace mgs {
+// Lets the other translation units of the library record a CUDA error for
+// mgs_last_cuda_error().
+void set_last_cuda_error(int code) { g_last_cuda = code; }
+}  // namespace mgs
+
 extern "C" {
 
 int mgs_version(void) { return 100; }
