@@ -20,6 +20,8 @@ HOST_LIBRARY = os.path.join(LIBDIR, "libddqd_host.so")
 SOURCES = ["api.cu", "mgs_dd.cu", "mgs_qd.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--fmad=false"]
+# extra nvcc flags for experiments (e.g. -DMGS_THREADS=256); empty by default
+EXTRA = os.environ.get("MGS_EXTRA_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     procs = []
     for src, obj in zip(SOURCES, objs):
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

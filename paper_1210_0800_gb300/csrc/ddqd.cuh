@@ -37,6 +37,10 @@ __device__ __forceinline__ long long bits_of(double a) { return __double_as_long
 __device__ __forceinline__ double rcp_rn(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
 __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ unsigned hi_word(double a) { return (unsigned)__double2hiint(a); }
+__device__ __forceinline__ double with_hi_word(double a, unsigned hi) {
+  return __hiloint2double((int)hi, __double2loint(a));
+}
 #else
 __host__ __device__ inline double fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 __host__ __device__ inline long long bits_of(double a) {
@@ -47,6 +51,13 @@ __host__ __device__ inline long long bits_of(double a) {
 __host__ __device__ inline double rcp_rn(double a) { return 1.0 / a; }
 __host__ __device__ inline double sqrt_rn(double a) { return std::sqrt(a); }
 __host__ __device__ inline double div_rn(double a, double b) { return a / b; }
+__host__ __device__ inline unsigned hi_word(double a) { return (unsigned)((unsigned long long)bits_of(a) >> 32); }
+__host__ __device__ inline double with_hi_word(double a, unsigned hi) {
+  unsigned long long b = ((unsigned long long)hi << 32) | ((unsigned long long)bits_of(a) & 0xffffffffULL);
+  double r;
+  std::memcpy(&r, &b, sizeof r);
+  return r;
+}
 #endif
 
 struct Fp {
@@ -58,11 +69,13 @@ struct Fp {
   __host__ __device__ __forceinline__ double fma(double a, double b, double c) const { return fma_rn(a, b, c); }
 };
 
-// |a| >= |b| for finite doubles, decided on the integer pipe.
+// Exponent order for fast two-sum: the sign-cleared high words (exponent and the top 20
+// mantissa bits) compared as unsigned integers.  If they are equal the exponents are
+// equal, which is all Dekker's condition needs.  Done on the high 32-bit words on
+// purpose: a 64-bit sign-masked compare is recognised as |a| >= |b| and compiled to
+// FP64-pipe instructions (measured: 2 extra per two-sum).
 __host__ __device__ __forceinline__ bool mag_ge(double a, double b) {
-  const unsigned long long m = 0x7fffffffffffffffULL;
-  return (static_cast<unsigned long long>(bits_of(a)) & m) >=
-         (static_cast<unsigned long long>(bits_of(b)) & m);
+  return (hi_word(a) & 0x7fffffffu) >= (hi_word(b) & 0x7fffffffu);
 }
 
 // s = fl(a + b), e = (a + b) - s exactly.  Orders the operands by magnitude, then runs
@@ -89,21 +102,13 @@ __host__ __device__ __forceinline__ void two_prod(const Fp& f, double a, double 
   e = f.fma(a, b, -p);
 }
 
-// v or -v, chosen on the integer pipe (a select of the sign bit; no FP64 instruction).
+// v or -v, chosen on the integer pipe (an exclusive-or of the sign bit in the high word).
 __host__ __device__ __forceinline__ double flip_if(double v, bool neg) {
-  long long b = bits_of(v) ^ (neg ? (long long)0x8000000000000000ULL : 0LL);
-  double r;
-#if defined(__CUDA_ARCH__)
-  r = __longlong_as_double(b);
-#else
-  std::memcpy(&r, &b, sizeof r);
-#endif
-  return r;
+  return with_hi_word(v, hi_word(v) ^ (neg ? 0x80000000u : 0u));
 }
 
 __host__ __device__ __forceinline__ bool finite64(double a) {
-  return (static_cast<unsigned long long>(bits_of(a)) & 0x7ff0000000000000ULL) !=
-         0x7ff0000000000000ULL;
+  return (hi_word(a) & 0x7ff00000u) != 0x7ff00000u;
 }
 
 // =====================================================================================

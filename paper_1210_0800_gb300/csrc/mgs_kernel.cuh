@@ -39,7 +39,10 @@ namespace mgs {
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ERANK = 2, ST_ENONFINITE = 3, ST_ETIMEOUT = 4 };
 
-constexpr int kThreads = 128;
+#ifndef MGS_THREADS
+#define MGS_THREADS 128
+#endif
+constexpr int kThreads = MGS_THREADS;
 
 struct Params {
   double* A;  // m x n, column-major by element, leading dimension lda (elements); Q on exit
