@@ -20,7 +20,7 @@ struct Plan {
   int L, m, n, nc, aug;
   int Br, Bc, h, w;
   size_t smem;
-  size_t off_sync, off_flags, off_P, off_V, off_Y, off_R, off_G, total, zero_bytes;
+  size_t off_sync, off_flags, off_P, off_V, off_Y, off_R, off_G, off_T, total, zero_bytes;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -82,6 +82,10 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   off = align256(off + sizeof(double) * (size_t)n * n * E);
   pl.off_G = off;  // G_kk, r_kk, 1/r_kk
   off = align256(off + sizeof(double) * 3 * (size_t)pl.nc * L);
+  pl.off_T = off;
+#if defined(MGS_TRACE) && MGS_TRACE
+  off = align256(off + sizeof(unsigned long long) * 8 * (size_t)(pl.nc + 1) * pl.Br * pl.Bc);
+#endif
   pl.total = off;
   return true;
 }
@@ -115,6 +119,7 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.b = aug ? b : nullptr;
   pr.R = R ? R : reinterpret_cast<double*>(wb + pl.off_R);
   pr.ldr = R ? ldr : n;
+  pr.Rt = reinterpret_cast<double*>(wb + pl.off_R);
   pr.x = aug ? x : nullptr;
   pr.z = aug ? z : nullptr;
   pr.m = m;
@@ -136,6 +141,11 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.one = 1.0;
   pr.nzero = -0.0;
   pr.timeout_ns = kTimeoutNs;
+#if defined(MGS_TRACE) && MGS_TRACE
+  pr.trace = reinterpret_cast<unsigned long long*>(wb + pl.off_T);
+#else
+  pr.trace = nullptr;
+#endif
   const int grid = pl.Br * pl.Bc;
   const int rc = (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st) : mgs::launch_qd(pr, grid, pl.smem, st);
   if (rc != 0) {
@@ -171,6 +181,19 @@ const char* mgs_status_string(int code) {
 }
 
 int mgs_last_cuda_error(void) { return g_last_cuda; }
+
+#if defined(MGS_TRACE) && MGS_TRACE
+// Trace builds only: where the phase timestamps sit in the workspace.
+__attribute__((visibility("default"))) int mgs_trace_layout(int limbs, int m, int n, int with_rhs,
+                                                            size_t* offset, int* steps, int* ctas) {
+  Plan pl;
+  if (!make_plan(limbs, m, n, with_rhs, pl)) return MGS_ENOSPACE;
+  *offset = pl.off_T;
+  *steps = pl.nc + 1;
+  *ctas = pl.Br * pl.Bc;
+  return MGS_OK;
+}
+#endif
 
 size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs) {
   Plan pl;

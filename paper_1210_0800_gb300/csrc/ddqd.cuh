@@ -146,6 +146,50 @@ struct DD {
     C = f.add(C, t);
   }
 
+  // One part (real or imaginary) of a dot-product accumulator: S + C.
+  struct pacc {
+    double S, C;
+  };
+  static constexpr int PACC = 2;
+  __host__ __device__ static __forceinline__ void pzero(pacc& a) { a.S = a.C = 0.0; }
+  // part 0: a += Re(conj(x) y) = xr yr + xi yi;  part 1: a += Im(conj(x) y) = xr yi - xi yr
+  __host__ __device__ static __forceinline__ void mac_part(const Fp& f, pacc& a, const elem& x, const elem& y,
+                                                          int part) {
+    const bool im = part != 0;
+    const double y1h = im ? y.v[2] : y.v[0], y1l = im ? y.v[3] : y.v[1];
+    const double y2h = im ? y.v[0] : y.v[2], y2l = im ? y.v[1] : y.v[3];
+    const double x2h = flip_if(x.v[2], im), x2l = flip_if(x.v[3], im);
+    term(f, a.S, a.C, x.v[0], x.v[1], y1h, y1l);
+    term(f, a.S, a.C, x2h, x2l, y2h, y2l);
+  }
+  // part 0: a += Re(r x) = rr xr - ri xi;  part 1: a += Im(r x) = rr xi + ri xr
+  __host__ __device__ static __forceinline__ void mul_acc_part(const Fp& f, pacc& a, const elem& r, const elem& x,
+                                                              int part) {
+    const bool im = part != 0;
+    const double x1h = im ? x.v[2] : x.v[0], x1l = im ? x.v[3] : x.v[1];
+    const double x2h = im ? x.v[0] : x.v[2], x2l = im ? x.v[1] : x.v[3];
+    const double r2h = flip_if(r.v[2], !im), r2l = flip_if(r.v[3], !im);
+    term(f, a.S, a.C, r.v[0], r.v[1], x1h, x1l);
+    term(f, a.S, a.C, r2h, r2l, x2h, x2l);
+  }
+  __host__ __device__ static __forceinline__ void pcombine(const Fp& f, pacc& a, const pacc& b) {
+    double s, t;
+    two_sum(f, a.S, b.S, s, t);
+    a.S = s;
+    a.C = f.add(f.add(a.C, b.C), t);
+  }
+  __host__ __device__ static __forceinline__ void pfinal(const Fp& f, const pacc& a, double* o) {
+    two_sum(f, a.S, a.C, o[0], o[1]);
+  }
+  // y := y - a for one part (y: L limbs)
+  __host__ __device__ static __forceinline__ void psub(const Fp& f, double* y, const pacc& a) {
+    double s, t;
+    two_sum(f, y[0], -a.S, s, t);
+    double lo = f.sub(y[1], a.C);
+    lo = f.add(lo, t);
+    two_sum(f, s, lo, y[0], y[1]);
+  }
+
   // acc += conj(x) * y   (x^H y convention)
   __host__ __device__ static __forceinline__ void mac_conj(const Fp& f, acc& a, const elem& x, const elem& y) {
     term(f, a.sr, a.cr, x.v[0], x.v[1], y.v[0], y.v[1]);
@@ -371,6 +415,51 @@ struct QD {
   __host__ __device__ static __forceinline__ void zero(acc& a) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) a.r.s[i] = a.i.s[i] = 0.0;
+  }
+
+  using pacc = part_t;
+  static constexpr int PACC = 4;
+  __host__ __device__ static __forceinline__ void pzero(pacc& a) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.s[i] = 0.0;
+  }
+  // part 0: a += xr yr + xi yi;  part 1: a += xr yi - xi yr
+  __host__ __device__ static __forceinline__ void mac_part(const Fp& f, pacc& a, const elem& x, const elem& y,
+                                                          int part) {
+    const bool im = part != 0;
+    double y1[4], y2[4], x2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      y1[i] = im ? y.v[4 + i] : y.v[i];
+      y2[i] = im ? y.v[i] : y.v[4 + i];
+      x2[i] = flip_if(x.v[4 + i], im);
+    }
+    prod(f, a, x.v, y1);
+    prod(f, a, x2, y2);
+  }
+  // part 0: a += rr xr - ri xi;  part 1: a += rr xi + ri xr
+  __host__ __device__ static __forceinline__ void mul_acc_part(const Fp& f, pacc& a, const elem& r, const elem& x,
+                                                              int part) {
+    const bool im = part != 0;
+    double x1[4], x2[4], r2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x1[i] = im ? x.v[4 + i] : x.v[i];
+      x2[i] = im ? x.v[i] : x.v[4 + i];
+      r2[i] = flip_if(r.v[4 + i], !im);
+    }
+    prod(f, a, r.v, x1);
+    prod(f, a, r2, x2);
+  }
+  __host__ __device__ static __forceinline__ void pcombine(const Fp& f, pacc& a, const pacc& b) { merge(f, a, b); }
+  __host__ __device__ static __forceinline__ void pfinal(const Fp& f, const pacc& a, double* o) { renorm(f, a, o); }
+  __host__ __device__ static __forceinline__ void psub(const Fp& f, double* y, const pacc& a) {
+    part_t t{{y[0], y[1], y[2], y[3]}};
+    put<0>(f, t, -a.s[0]);
+    put<1>(f, t, -a.s[1]);
+    put<2>(f, t, -a.s[2]);
+    put<3>(f, t, -a.s[3]);
+    renorm(f, t, y);
   }
 
   __host__ __device__ static __forceinline__ void mac_conj(const Fp& f, acc& a, const elem& x, const elem& y) {

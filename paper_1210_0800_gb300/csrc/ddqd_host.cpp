@@ -48,6 +48,34 @@ void dot(int n, int split, const double* x, const double* y, double* out, bool n
   store<Ar>(out, Ar::finalize(kFp, a));
 }
 
+template <class Ar>
+void dot_parts(int n, int split, const double* x, const double* y, double* out) {
+  const int E = 2 * Ar::L;
+  for (int part = 0; part < 2; ++part) {
+    typename Ar::pacc a, b;
+    Ar::pzero(a);
+    Ar::pzero(b);
+    for (int i = 0; i < n; ++i) Ar::mac_part(kFp, (i < split) ? a : b, load<Ar>(x + i * E), load<Ar>(y + i * E), part);
+    Ar::pcombine(kFp, a, b);
+    Ar::pfinal(kFp, a, out + part * Ar::L);
+  }
+}
+
+// out = y - sum_i r_i x_i (complex), through part accumulators
+template <class Ar>
+void axpy_parts(int n, const double* y, const double* r, const double* x, double* out) {
+  const int E = 2 * Ar::L;
+  for (int part = 0; part < 2; ++part) {
+    typename Ar::pacc a;
+    Ar::pzero(a);
+    for (int i = 0; i < n; ++i) Ar::mul_acc_part(kFp, a, load<Ar>(r + i * E), load<Ar>(x + i * E), part);
+    double yy[4];
+    for (int q = 0; q < Ar::L; ++q) yy[q] = y[part * Ar::L + q];
+    Ar::psub(kFp, yy, a);
+    for (int q = 0; q < Ar::L; ++q) out[part * Ar::L + q] = yy[q];
+  }
+}
+
 }  // namespace
 
 #define EXPORT extern "C" __attribute__((visibility("default")))
@@ -104,4 +132,17 @@ EXPORT void h_sqrt(int L, const double* s, double* out) {
     store_real<mgs::DD>(out, mgs::DD::sqrt(kFp, load_real<mgs::DD>(s)));
   else
     store_real<mgs::QD>(out, mgs::QD::sqrt(kFp, load_real<mgs::QD>(s)));
+}
+
+EXPORT void h_dot_parts(int L, int n, int split, const double* x, const double* y, double* out) {
+  if (L == 2)
+    dot_parts<mgs::DD>(n, split, x, y, out);
+  else
+    dot_parts<mgs::QD>(n, split, x, y, out);
+}
+EXPORT void h_axpy_parts(int L, int n, const double* y, const double* r, const double* x, double* out) {
+  if (L == 2)
+    axpy_parts<mgs::DD>(n, y, r, x, out);
+  else
+    axpy_parts<mgs::QD>(n, y, r, x, out);
 }

@@ -50,6 +50,8 @@ struct Params {
   double* b;  // m elements (augmented column) or nullptr for a plain QR
   double* R;  // n x n, leading dimension ldr (elements)
   long long ldr;
+  double* Rt;  // n x n (leading dimension n) scaled columns r_jk / r_kk for back substitution;
+               // the same memory as R when the caller does not want R
   double* x;  // n elements (solution) or nullptr
   double* z;  // L doubles (residual norm) or nullptr
   int m, n, nc, aug;
@@ -65,7 +67,21 @@ struct Params {
   int* status;
   double one, nzero;
   long long timeout_ns;
+  unsigned long long* trace;  // phase timestamps, (nc + 1) x grid x 8 (trace builds only)
 };
+
+// Phase timestamps for performance analysis (compiled in with -DMGS_TRACE=1 only).
+#if defined(MGS_TRACE) && MGS_TRACE
+#define MGS_TR(step, ph)                                                                    \
+  do {                                                                                     \
+    if (threadIdx.x == 0 && pr.trace)                                                      \
+      pr.trace[((size_t)(step) * gridDim.x + blockIdx.x) * 8 + (ph)] = globaltimer();       \
+  } while (0)
+#else
+#define MGS_TR(step, ph) \
+  do {                   \
+  } while (0)
+#endif
 
 // ------------------------------------------------------------------ memory-model helpers
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -221,7 +237,8 @@ __host__ __device__ inline size_t smem_bytes(int L, int h, int w) {
   const size_t E = 2 * (size_t)L;
   return sizeof(double) * ((size_t)(w + 2) * E * h  // tile + two pivot buffers
                            + (size_t)(w + 1) * E     // coefficients + pivot norm
-                           + 4 * E)                  // scalars
+                           + 4 * E                   // scalars
+                           + (size_t)kThreads * L)   // partial-sum reduction tree
          + 16 * sizeof(int);
 }
 
@@ -250,7 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   double* coef = piv + (size_t)2 * E * h;    // w * E
   double* gkk = coef + (size_t)w * E;        // E (pivot norm, as an element)
   double* scal = gkk + E;                    // 4 * E scratch
-  int* iflag = reinterpret_cast<int*>(scal + 4 * E);
+  double* redb = scal + 4 * E;               // kThreads part accumulators
+  int* iflag = reinterpret_cast<int*>(redb + (size_t)kThreads * L);
+  using pacc = typename Ar::pacc;
+  constexpr int PACC = Ar::PACC;
+  static_assert(sizeof(pacc) == PACC * sizeof(double) && PACC == L, "part accumulator layout");
 
   auto col_of = [&](int s) { return c + s * Bc; };
   auto colptr = [&](int j, int i) -> double* {
@@ -304,39 +325,51 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   if (tid == 0 && iflag[0]) set_status(pr.status, ST_ENONFINITE);
 
   // Partials of the Gram row of pivot `kp` (pivot rows in pivbuf) for own columns j >= kp,
-  // written to P[buf].  g lanes share one column; lanes stride over the rows.
+  // written to P[buf].  Work items are (column, part, row chunk): all lanes get about the
+  // same number of rows; the chunks of one (column, part) are combined by a tree in
+  // shared memory.  For the pivot column only the real part (its norm) is formed.
   auto partials = [&](int kp, const double* pivbuf, int buf) {
     const int s0 = (kp - c + Bc - 1) / Bc;  // first slot with column >= kp
     const int first = max(s0, 0);
     const int nact = w - first;
     if (nact <= 0) return;
-    int g = pow2_floor(kThreads / nact);
-    g = min(g, 32);
-    g = min(g, pow2_ceil(max(hr, 1)));
-    const int groups = kThreads / g;
-    const int gi = tid / g, gl = tid % g;
-    for (int base = 0; base < nact; base += groups) {
-      const int s = first + base + gi;
-      acc a;
-      Ar::zero(a);
-      const bool act = (base + gi) < nact;
+    const int pairs = 2 * nact;
+    int C = kThreads / pairs;
+    C = max(1, min(C, max(hr, 1)));
+    const int per_round = kThreads / C;
+    pacc* red = reinterpret_cast<pacc*>(redb);
+    for (int base = 0; base < pairs; base += per_round) {
+      const int job = tid / C, ch = tid % C;
+      const int pi = base + job;
+      const bool act = job < per_round && pi < pairs;
+      const int s = first + (pi >> 1), part = pi & 1;
+      pacc a;
+      Ar::pzero(a);
       if (act) {
         const int j = col_of(s);
-        const double* ts = tile + (size_t)s * E * h;
-        if (j == kp) {
-          for (int l = gl; l < hr; l += g) Ar::mac_norm(f, a, sm_load<Ar>(ts, h, l));
-        } else {
-          for (int l = gl; l < hr; l += g) Ar::mac_conj(f, a, sm_load<Ar>(pivbuf, h, l), sm_load<Ar>(ts, h, l));
+        if (!(j == kp && part == 1)) {
+          const double* ts = tile + (size_t)s * E * h;
+          for (int l = ch; l < hr; l += C) Ar::mac_part(f, a, sm_load<Ar>(pivbuf, h, l), sm_load<Ar>(ts, h, l), part);
         }
       }
-      for (int off = 1; off < g; off <<= 1) {
-        const acc o = acc_shfl_xor<Ar>(a, off);
-        Ar::combine(f, a, o);
+      red[tid] = a;
+      __syncthreads();
+      for (int st = 1; st < C; st <<= 1) {
+        if (act && (ch % (2 * st)) == 0 && ch + st < C) {
+          pacc x = red[tid];
+          Ar::pcombine(f, x, red[tid + st]);
+          red[tid] = x;
+        }
+        __syncthreads();
       }
-      if (act && gl == 0) {
+      if (act && ch == 0) {
         const int j = col_of(s);
-        acc_store<Ar>(pr.P + (((size_t)buf * Br + p) * nc + j) * ACC, a);
+        const double* src = reinterpret_cast<const double*>(&red[tid]);
+        double* dst = pr.P + (((size_t)buf * Br + p) * nc + j) * ACC + part * PACC;
+#pragma unroll
+        for (int q = 0; q < PACC; ++q) dst[q] = src[q];
       }
+      __syncthreads();
     }
   };
 
@@ -354,36 +387,49 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     const int s0 = (k + 1 - c + Bc - 1) / Bc;  // first slot with column > k
     const int first = max(s0, 0);
     const int nact = w - first;                // own columns j > k
+    MGS_TR(k, 0);
 
-    // (1) reduce the Br partials of the pivot norm and of the own columns j > k
+    // (1) reduce the Br partials of the pivot norm and of the own columns j > k, one lane
+    //     per (column, part, row block); a shuffle tree over the row blocks
     {
       const int BrP = pow2_ceil(Br);
       const int nred = 1 + max(nact, 0);
-      const int jobs = nred * BrP;
+      const int jobs = nred * 2 * BrP;
       for (int base = 0; base < jobs; base += kThreads) {
         const int job = base + tid;
-        const int ci = job / BrP, pp = job % BrP;
-        acc a;
-        Ar::zero(a);
-        const bool act = job < jobs && pp < Br;
-        if (act) {
+        const int ci = job / (2 * BrP), rem = job % (2 * BrP);
+        const int part = rem / BrP, pp = rem % BrP;
+        const bool want = job < jobs && !(ci == 0 && part == 1);
+        pacc a;
+        Ar::pzero(a);
+        if (want && pp < Br) {
           const int j = (ci == 0) ? k : col_of(first + ci - 1);
-          a = acc_load_cg<Ar>(pr.P + (((size_t)cur * Br + pp) * nc + j) * ACC);
+          const double* src = pr.P + (((size_t)cur * Br + pp) * nc + j) * ACC + part * PACC;
+          double* d = reinterpret_cast<double*>(&a);
+#pragma unroll
+          for (int q = 0; q < PACC; ++q) d[q] = __ldcg(src + q);
         }
         for (int off = 1; off < BrP; off <<= 1) {
-          const acc o = acc_shfl_xor<Ar>(a, off);
-          Ar::combine(f, a, o);
+          pacc o;
+          const double* sa = reinterpret_cast<const double*>(&a);
+          double* so = reinterpret_cast<double*>(&o);
+#pragma unroll
+          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], off);
+          Ar::pcombine(f, a, o);
         }
         if (job < jobs && pp == 0) {
-          const elem g = Ar::finalize(f, a);
-          double* dst = (ci == 0) ? gkk : coef + (size_t)(first + ci - 1) * E;
+          double* dst = ((ci == 0) ? gkk : coef + (size_t)(first + ci - 1) * E) + part * L;
+          if (want) {
+            Ar::pfinal(f, a, dst);
+          } else {
 #pragma unroll
-          for (int q = 0; q < E; ++q) dst[q] = g.v[q];
+            for (int q = 0; q < L; ++q) dst[q] = 0.0;
+          }
         }
       }
     }
     __syncthreads();
-
+    MGS_TR(k, 1);
     // pivot norm G_kk (identical in every CTA)
     elem gk;
 #pragma unroll
@@ -425,6 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     }
     __syncthreads();
 
+    MGS_TR(k, 2);
     // (3) look-ahead: update column k+1 first and publish its rows
     if (own_k1) {
       const int s1 = (k + 1) / Bc;
@@ -456,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       }
     }
 
+    MGS_TR(k, 3);
     // (4) update the other own columns j > k+1 (one lane per element part)
     {
       const int sb = own_k1 ? first + 1 : first;  // slot of column k+1 is `first` when owned
@@ -477,6 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       }
     }
 
+    MGS_TR(k, 4);
     // (5) coefficients of row k go to R (row k) and Y (column b); scaled by r_kk at the end
     if (p == 0) {
       for (int t = tid; t < nact; t += kThreads) {
@@ -502,11 +551,14 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     }
     __syncthreads();
 
+    MGS_TR(k, 5);
     // (7) partials of step k+1
     partials(k + 1, pnxt, nxt);
+    MGS_TR(k, 6);
     grid_barrier(pr, epoch);
   }
   grid_barrier(pr, epoch);
+  MGS_TR(nc, 0);
 
   // ---------------------------------------------------------------- normalisation
   const int nthreads = gridDim.x * kThreads;
@@ -520,6 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     if (pr.aug && k == nc - 1 && pr.z) st_real(pr.z, r);
   }
   grid_barrier(pr, epoch);
+  MGS_TR(nc, 1);
   // (E2) q_j = a_j / r_jj for the own columns (the tile holds the unnormalised columns)
   {
     const int nq = pr.n;  // columns that are normalised
@@ -566,10 +619,36 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   // ---------------------------------------------------------------- back substitution
   if (!pr.aug || pr.x == nullptr) return;
   grid_barrier(pr, epoch);
-  // Figure 3, column by column, in blocks of kBS rows: CTA 0 runs the chain of the
-  // diagonal block (x_k = y_k / r_kk as y_k * (1/r_kk); y_j -= r_jk x_k for the block's
-  // rows j < k); then every CTA applies the block's x to the rows above it.
+  // Figure 3 on the column-scaled system: with D = diag(r_kk), R x = y is solved as
+  // (R D^-1)(D x) = y.  The scaled columns t_jk = r_jk / r_kk are formed once, in parallel;
+  // the sequential chain is then x~_k = y_k and y_j -= t_jk x~_k (one update per link
+  // instead of a product and an update), and x_k = x~_k / r_kk (a true division) for all k
+  // in parallel at the end.
   const int n = pr.n;
+  {
+    const long long tot = (long long)n * (n - 1);  // (j < k) pairs x 2 parts
+    for (long long idx = gtid; idx < tot; idx += nthreads) {
+      const int part = (int)(idx & 1);
+      const long long pi = idx >> 1;
+      int k = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pi)) * 0.5);  // pi = k(k-1)/2 + j
+      while ((long long)k * (k - 1) / 2 > pi) --k;
+      while ((long long)(k + 1) * k / 2 <= pi) ++k;
+      const int j = (int)(pi - (long long)k * (k - 1) / 2);
+      elem r;
+#pragma unroll
+      for (int q = 0; q < E; ++q) r.v[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < L; ++q) r.v[part * L + q] = __ldcg(pr.R + ((size_t)k * pr.ldr + j) * E + part * L + q);
+      elem t = r;
+      Ar::mul_real_part(f, t, r, ld_real(pr.Ri + (size_t)k * L), part);
+#pragma unroll
+      for (int q = 0; q < L; ++q) pr.Rt[((size_t)k * n + j) * E + part * L + q] = t.v[part * L + q];
+    }
+  }
+  grid_barrier(pr, epoch);
+  MGS_TR(nc, 2);
+  // blocks of kBS rows: CTA 0 runs the chain of the diagonal block, then every CTA
+  // applies the block's x~ to the rows above it.
   for (int e = n; e > 0; e -= kBS) {
     const int s = max(0, e - kBS);
     if (blockIdx.x == 0) {
@@ -581,26 +660,15 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       }
       __syncthreads();
       for (int k = e - 1; k >= s; --k) {
-        double* yk = ys + (size_t)(k - s) * E;
-        if (tid < 2) {
-          const elem y = sm_load_part<Ar>(yk, 1, 0, tid);
-          elem x = y;
-          Ar::mul_real_part(f, x, y, ld_real(pr.Ri + (size_t)k * L), tid);
-#pragma unroll
-          for (int q = 0; q < L; ++q) {
-            yk[tid * L + q] = x.v[tid * L + q];  // x_k replaces y_k
-            pr.x[(size_t)k * E + tid * L + q] = x.v[tid * L + q];
-          }
-        }
-        __syncthreads();
         elem xk;
 #pragma unroll
-        for (int q = 0; q < E; ++q) xk.v[q] = yk[q];
+        for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
+        if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
         for (int t = tid; t < 2 * (k - s); t += kThreads) {
           const int j = s + (t >> 1), part = t & 1;
           double* yj = ys + (size_t)(j - s) * E;
           elem y = sm_load_part<Ar>(yj, 1, 0, part);
-          Ar::update_part(f, y, g_load_cg<Ar>(pr.R + ((size_t)k * pr.ldr + j) * E), xk, part);
+          Ar::update_part(f, y, g_load_cg<Ar>(pr.Rt + ((size_t)k * n + j) * E), xk, part);
 #pragma unroll
           for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
         }
@@ -609,25 +677,59 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     }
     if (s == 0) break;
     grid_barrier(pr, epoch);
-    // rows j < s: y_j -= sum_{k in [s, e)} r_jk x_k, one (row, part) per lane
+    // rows j < s: y_j -= sum_{k in [s, e)} t_jk x~_k; 8 lanes per (row, part) each sum a
+    // share of the terms, a shuffle tree combines them, lane 0 of the group subtracts
     {
-      const int tot = s * 2;
-      for (int idx = gtid; idx < tot; idx += nthreads) {
-        const int j = idx >> 1, part = idx & 1;
-        elem y;
+      constexpr int G = 8;
+      const int tot = s * 2 * G;
+      const int span = ((tot + nthreads - 1) / nthreads) * nthreads;  // uniform trip count
+      for (int idx = gtid; idx < span; idx += nthreads) {
+        const bool act = idx < tot;
+        const int grp = idx / G, ch = idx % G;
+        const int j = grp >> 1, part = grp & 1;
+        pacc a;
+        Ar::pzero(a);
+        if (act)
+          for (int k = e - 1 - ch; k >= s; k -= G)
+            Ar::mul_acc_part(f, a, g_load_cg<Ar>(pr.Rt + ((size_t)k * n + j) * E),
+                             g_load_cg<Ar>(pr.x + (size_t)k * E), part);
+        for (int off = 1; off < G; off <<= 1) {
+          pacc o;
+          const double* sa = reinterpret_cast<const double*>(&a);
+          double* so = reinterpret_cast<double*>(&o);
 #pragma unroll
-        for (int q = 0; q < E; ++q) y.v[q] = 0.0;
+          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], off);
+          Ar::pcombine(f, a, o);
+        }
+        if (act && ch == 0) {
+          double y[L];
+          double* yp = pr.Y + (size_t)j * E + part * L;
 #pragma unroll
-        for (int q = 0; q < L; ++q) y.v[part * L + q] = __ldcg(pr.Y + (size_t)j * E + part * L + q);
-        for (int k = e - 1; k >= s; --k)
-          Ar::update_part(f, y, g_load_cg<Ar>(pr.R + ((size_t)k * pr.ldr + j) * E),
-                          g_load_cg<Ar>(pr.x + (size_t)k * E), part);
+          for (int q = 0; q < L; ++q) y[q] = __ldcg(yp + q);
+          Ar::psub(f, y, a);
 #pragma unroll
-        for (int q = 0; q < L; ++q) pr.Y[(size_t)j * E + part * L + q] = y.v[part * L + q];
+          for (int q = 0; q < L; ++q) yp[q] = y[q];
+        }
       }
     }
     grid_barrier(pr, epoch);
   }
+  grid_barrier(pr, epoch);
+  // x_k = x~_k / r_kk
+  for (int idx = gtid; idx < 2 * n; idx += nthreads) {
+    const int k = idx >> 1, part = idx & 1;
+    elem xt;
+#pragma unroll
+    for (int q = 0; q < E; ++q) xt.v[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) xt.v[part * L + q] = __ldcg(pr.x + (size_t)k * E + part * L + q);
+    const real r = ld_real(pr.Rd + (size_t)k * L);
+    elem xv = xt;
+    Ar::div_real_part(f, xv, xt, r, Ar::inv_lead(r), part);
+#pragma unroll
+    for (int q = 0; q < L; ++q) pr.x[(size_t)k * E + part * L + q] = xv.v[part * L + q];
+  }
+  MGS_TR(nc, 3);
 }
 
 }  // namespace mgs

@@ -27,6 +27,8 @@ def hl():
     lib.h_sqrt.argtypes = [i, dp, dp]
     lib.h_two_sum.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp]
     lib.h_two_prod.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp]
+    lib.h_dot_parts.argtypes = [i, i, i, dp, dp, dp]
+    lib.h_axpy_parts.argtypes = [i, i, dp, dp, dp, dp]
     return lib
 
 
@@ -159,3 +161,42 @@ def test_sqrt(hl, L):
         hl.h_sqrt(L, sp, op)
         fs, r = pins.fval(s), pins.fval(oa)
         assert r > 0 and abs(r * r - fs) <= 8 * U[L] * fs, float((r * r - fs) / fs)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("n,split", [(1, 0), (9, 4), (64, 31)])
+def test_dot_parts(hl, L, n, split):
+    """Real and imaginary parts of x^H y accumulated separately (as the kernels' lanes do)."""
+    x, y = cplx(L, 800 + n, n), cplx(L, 900 + n, n)
+    out = np.zeros((2, L))
+    _, xp = P(x)
+    _, yp = P(y)
+    oa, op = P(out)
+    hl.h_dot_parts(L, n, split, xp, yp, op)
+    ex = (F(0), F(0))
+    scale = 0.0
+    for i in range(n):
+        a, b = pins.cval(x[i]), pins.cval(y[i])
+        ex = pins.cadd(ex, pins.cmul(pins.cconj(a), b))
+        scale += math.sqrt(float(pins.cabs2(a)) * float(pins.cabs2(b)))
+    assert pins.cnorm_inf(pins.csub(pins.cval(oa), ex)) <= 4 * (n + 2) * UNIT[L] * scale
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("n", [1, 5, 32])
+def test_axpy_parts(hl, L, n):
+    """y - sum_i r_i x_i with part accumulators (the back-substitution update)."""
+    y, r, x = cplx(L, 1000 + n, 1), cplx(L, 1100 + n, n), cplx(L, 1200 + n, n)
+    out = np.zeros((2, L))
+    _, yp = P(y[0])
+    _, rp = P(r)
+    _, xp = P(x)
+    oa, op = P(out)
+    hl.h_axpy_parts(L, n, yp, rp, xp, op)
+    ex = pins.cval(y[0])
+    scale = math.sqrt(float(pins.cabs2(ex)))
+    for i in range(n):
+        a, b = pins.cval(r[i]), pins.cval(x[i])
+        ex = pins.csub(ex, pins.cmul(a, b))
+        scale += math.sqrt(float(pins.cabs2(a)) * float(pins.cabs2(b)))
+    assert pins.cnorm_inf(pins.csub(pins.cval(oa), ex)) <= 4 * (n + 2) * UNIT[L] * scale
