@@ -76,6 +76,34 @@ def peak_fp64_ops_per_s(sm_max_mhz: float) -> float:
     return SMS * FP64_LANES_PER_CLK_SM * sm_max_mhz * 1e6
 
 
+def kernel_source_sha() -> str:
+    """Hash of the CUDA sources (the ncu traffic figure is valid for this hash only)."""
+    import glob
+    import hashlib
+
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_0800_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_1210_0800_gb300", "csrc", "*.cuh")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch from the committed ncu capture, or None when the kernel
+    sources changed since that capture (or the workload was not captured)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return t.get("traffic_bytes_per_launch", {}).get(workload)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -291,7 +319,8 @@ def run_gpu(args, L, m, n, extreme, rank, world):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": K,
         "roofline": {"bound": "alu", "achieved": 2 * achieved_ops / 1e12, "peak": 2 * peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops,
+                     "traffic": measured_traffic(args.workload),
                      "note": "FP64 pipe: algorithmic FP64 instructions of the kernel's primitives per solve "
                              "(%.4g) / CUDA-event time per solve; each instruction counted as one FMA slot "
                              "(2 flops) like the peak (152 SMs x 2 DFMA/clk x %.0f MHz)" % (ops, sm_max)},
