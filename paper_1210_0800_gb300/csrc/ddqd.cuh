@@ -548,33 +548,40 @@ struct QD {
 
   __host__ __device__ static __forceinline__ double inv_lead(const real& r) { return rcp_rn(r.x[0]); }
 
-  // a / r: five quotient digits, each from the leading part of the exactly tracked
-  // remainder (long division), then renormalised.
+  // a / r: long division with an exactly tracked remainder.  inv ~ 1/r.x[0] is refined
+  // to a double-double reciprocal (one Newton correction), which yields two 104-bit
+  // double-double quotient digits; a last 53-bit digit takes the error below 2^-210.
   __host__ __device__ static __forceinline__ void div_part(const Fp& f, const double* a, const real& r, double inv,
-                                                  double* q) {
+                                                           double* q) {
+    double e = f.fma(-r.x[0], inv, f.one);  // 1 - r inv, exact enough: |e| ~ 2^-53
+    e = f.fma(-r.x[1], inv, e);
+    const double ilo = f.mul(inv, e);  // (inv, ilo) ~ 1/r to 2^-104
     part_t rem{{a[0], a[1], a[2], a[3]}};
-    double d[5];
+    double d[4];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      // the remainder is a normalised expansion here, so its leading limb is accurate
-      const double qk = f.mul(rem.s[0], inv);
-      d[k] = qk;
-      if (k < 4) {
-        const double nq = -qk;
-        put_prod<0>(f, rem, nq, r.x[0]);
-        put_prod<1>(f, rem, nq, r.x[1]);
-        put_prod<2>(f, rem, nq, r.x[2]);
-        rem.s[3] = f.fma(nq, r.x[3], rem.s[3]);
-        renorm(f, rem, rem.s);  // subtracting q_k r cancels the leading levels
-      }
+    for (int t = 0; t < 2; ++t) {
+      // double-double digit: leading two limbs of the (normalised) remainder times (inv, ilo)
+      double p, pe, qh, ql;
+      two_prod(f, rem.s[0], inv, p, pe);
+      pe = f.fma(rem.s[0], ilo, pe);
+      pe = f.fma(rem.s[1], inv, pe);
+      fast_two_sum(f, p, pe, qh, ql);
+      d[2 * t] = qh;
+      d[2 * t + 1] = ql;
+      // rem -= (qh + ql) r, terms of order 0..3
+      put_prod<0>(f, rem, -qh, r.x[0]);
+      put_prod<1>(f, rem, -qh, r.x[1]);
+      put_prod<1>(f, rem, -ql, r.x[0]);
+      put_prod<2>(f, rem, -qh, r.x[2]);
+      put_prod<2>(f, rem, -ql, r.x[1]);
+      rem.s[3] = f.fma(-qh, r.x[3], rem.s[3]);
+      rem.s[3] = f.fma(-ql, r.x[2], rem.s[3]);
+      renorm(f, rem, rem.s);  // the leading levels cancel; renormalise for the next digit
     }
-    // sum the digits into a normalised expansion
-    part_t s{{d[0], 0.0, 0.0, 0.0}};
-    put<0>(f, s, d[1]);
-    put<0>(f, s, d[2]);
-    put<1>(f, s, d[3]);
-    put<1>(f, s, d[4]);
-    renorm(f, s, q);
+    // digits sit at levels 0..3; the last single digit is below level 3
+    part_t sq{{d[0], d[1], d[2], d[3]}};
+    sq.s[3] = f.add(sq.s[3], f.mul(rem.s[0], inv));
+    renorm(f, sq, q);
   }
   __host__ __device__ static __forceinline__ elem div_real(const Fp& f, const elem& a, const real& r, double inv) {
     elem q;
