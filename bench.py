@@ -47,6 +47,11 @@ WORKLOADS = {
     "qd_512": (4, 512, 512, False),
 }
 DEFAULT = "c1_qd_320x256"
+# batched workloads: name -> (limbs, batch, n range, extra rows range)
+BATCHED = {
+    "c3_dd_batched_512": (2, 512, (16, 192), (0, 16)),
+    "qd_batched_512": (4, 512, (16, 192), (0, 16)),
+}
 
 # FP64 pipe instructions of the kernels' primitives (static counts of csrc/ddqd.cuh):
 # complex conjugated multiply-accumulate, complex update y -= c x, |x|^2 accumulate,
@@ -336,23 +341,179 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     return 0
 
 
+def make_batch_host(L, batch, n_rng, e_rng, seed):
+    ms, ns = inputs.ragged_shapes(batch, seed, n_rng[0], n_rng[1], e_rng[0], e_rng[1])
+    systems = []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        A, _, b = inputs.system(int(m), int(n), L, inputs.system_seed(seed, i))
+        systems.append((A, b))
+    return systems
+
+
+def run_gpu_batched(args, rank, world):
+    """One step = one launch solving a ragged batch of independent systems (replayed from
+    a CUDA graph); every step works on its own, distinct batch resident in HBM."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+    from paper_1210_0800_gb300 import tune as tuner
+
+    L, batch, n_rng, e_rng = BATCHED[args.workload]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    seed0 = inputs.BASE_SEED + 3
+    host = make_batch_host(L, batch, n_rng, e_rng, inputs.system_seed(seed0, rank))
+    ops = sum(fp64_ops(L, A.shape[1], A.shape[0]) for A, _ in host)
+    # distinct device copies of the batch for warm-up + timed steps (pools are overwritten)
+    base = mg.make_batch(host, dev)
+    best, times = tuner.tune_batched(base, reps=1)
+    batches = [mg.Batch(base.A_pool.clone(), base.b_pool.clone(), base.x_pool.clone(), base.a_off, base.b_off,
+                        base.x_off, base.m, base.n, base.max_m, base.max_n, base.order) for _ in range(K + W)]
+    need = mg._binding.batched_workspace_bytes(L, batch, base.max_m, base.max_n, best)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    st = torch.zeros((K + W, batch), dtype=torch.int32, device=dev)
+    # capture one graph per batch copy
+    graphs = []
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for i in range(K + W):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                mg.ls_solve_batched(batches[i], workspace=ws, status=st[i], tune=best)
+            graphs.append(g)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    for i in range(W):
+        graphs[i].replay()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0e.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        graphs[W + i].replay()
+        ev[i][1].record(stream)
+    t1e.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms_total = t0e.elapsed_time(t1e)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    bad = int((st[W:] != 0).sum().item())
+    # end to end: pinned host pools -> device, solve, x pool -> host
+    Ah, bh = base.A_pool.cpu().pin_memory(), base.b_pool.cpu().pin_memory()
+    xh = torch.empty_like(base.x_pool, device="cpu").pin_memory()
+    work = batches[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ke = 3
+    e0.record(stream)
+    for _ in range(Ke):
+        work.A_pool.copy_(Ah, non_blocking=True)
+        work.b_pool.copy_(bh, non_blocking=True)
+        mg.ls_solve_batched(work, workspace=ws, status=st[0], tune=best)
+        xh.copy_(work.x_pool, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / Ke
+    # the same systems solved one after another with the single-system solve
+    fn = mg.ls_solve_dd if L == 2 else mg.ls_solve_qd
+    nseq = min(batch, args.seq_sample)
+    sel = list(range(0, batch, max(1, batch // nseq)))[:nseq]
+    Ad = [torch.from_numpy(host[i][0]).to(dev) for i in sel]
+    bd = [torch.from_numpy(host[i][1]).to(dev) for i in sel]
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for A_, b_ in zip(Ad, bd):
+        fn(A_, b_)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = s0.elapsed_time(s1)
+    seq_ops = sum(fp64_ops(L, host[i][0].shape[1], host[i][0].shape[0]) for i in sel)
+    if rank != 0:
+        return 0
+    value = world * batch * K / (ms_total / 1000.0)
+    peaks = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = peak_fp64_ops_per_s(sm_max)
+    achieved = ops / (kernel_ms / 1000.0)
+    h2d = (base.A_pool.numel() + base.b_pool.numel()) * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "limbs": L, "systems_per_step": batch, "n_range": list(n_rng),
+                   "m_minus_n_range": list(e_rng), "max_m": base.max_m, "max_n": base.max_n,
+                   "launch": "one persistent launch per step, replayed from a CUDA graph",
+                   "tune": {"threads": best[0], "ctas_per_sm": best[1], "candidates_ms": times},
+                   "l2": "inputs larger than L2 (every step a distinct %.0f MB batch)" % (h2d / 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": world * batch / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": base.x_pool.numel() * 8},
+        "gpu_launches": K,
+        "roofline": {"bound": "alu", "achieved": 2 * achieved / 1e12, "peak": 2 * peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": measured_traffic(args.workload),
+                     "note": "FP64 pipe: algorithmic FP64 instructions of all systems (%.4g) per launch / "
+                             "CUDA-event time per launch" % ops},
+        "kernel_ms": kernel_ms,
+        "sequential_plain": {"value": len(sel) / (seq_ms / 1000.0), "unit": "systems/s",
+                             "systems": len(sel), "frac": (seq_ops / (seq_ms / 1000.0)) / peak_ops,
+                             "note": "the same systems (every %d-th) solved one after another with the "
+                                     "single-system solve on the same GPU" % max(1, batch // nseq)},
+        "status_errors": bad,
+    }
+    if clk:
+        line["clocks"] = clk
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.get()
+        small = sorted(range(batch), key=lambda i: host[i][0].shape[0])[:8]
+        t0 = time.perf_counter()
+        for i in small:
+            o.ls_solve(host[i][0].copy(), host[i][1].copy())
+        dt = time.perf_counter() - t0
+        frac_work = sum(fp64_ops(L, host[i][0].shape[1], host[i][0].shape[0]) for i in small) / ops
+        line["cpu_baseline"] = {"value": batch * frac_work / dt, "unit": "systems/s", "cores": 1, "kind": "oracle",
+                                "sample": "oracle ls_solve of the 8 smallest systems of the batch (%.2f s), scaled "
+                                          "by their share %.5f of the batch's FP64 operations" % (dt, frac_work)}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCHED))
+    ap.add_argument("--seq-sample", type=int, default=64, help="systems solved one by one for the comparison")
     ap.add_argument("--ref-seconds", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
-    L, m, n, extreme = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1 and args.impl == "ours":
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    if args.workload in BATCHED:
+        if args.impl == "reference":
+            L, batch, n_rng, e_rng = BATCHED[args.workload]
+            return run_reference(args, L, (n_rng[0] + n_rng[1]) // 2 + 8, (n_rng[0] + n_rng[1]) // 2, rank, world)
+        return run_gpu_batched(args, rank, world)
+    L, m, n, extreme = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, L, m, n, rank, world)
     return run_gpu(args, L, m, n, extreme, rank, world)

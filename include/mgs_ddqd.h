@@ -101,6 +101,40 @@ int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, do
                 void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 
 /*
+ * Batched least squares: `batch` independent systems of different sizes in one launch
+ * (many paths tracked at once; the paper solves one system at a time, Section 2, and
+ * its related work [ASK12] studies many small independent QR factorisations).  Each
+ * system is the ls_solve_* of Section 3 (Figure 1, Eq. 1) and Section 6 (Figure 3).
+ *   A_pool, b_pool, x_pool   element pools (device); system i uses
+ *       A_pool + a_off[i]*2L  (m[i] x n[i], column-major, leading dimension m[i]; Q on exit)
+ *       b_pool + b_off[i]*2L  (m[i] elements; the residual on exit)
+ *       x_pool + x_off[i]*2L  (n[i] elements, output)
+ *   a_off, b_off, x_off  device int64 arrays of element offsets (8-byte aligned)
+ *   m, n                 device int32 arrays of sizes (1 <= n[i] <= m[i] <= max_m, n[i] <= max_n)
+ *   order                optional device int32 permutation: the order in which systems are
+ *                        handed out (largest first balances the work); NULL = 0, 1, 2, ...
+ *   dev_status           device int32 array of `batch` words: per-system status
+ *                        (MGS_OK, MGS_EINVAL for a bad size, MGS_ERANK, MGS_ENONFINITE)
+ *   tune                 optional launch shape (NULL or zero fields = defaults)
+ * Workspace: mgs_batched_workspace_bytes(limbs, batch, max_m, max_n, tune).
+ * One CTA solves one system at a time; no CTA waits for another.
+ */
+typedef struct {
+  int threads;     /* threads per CTA: 128 or 256 (0 = 128) */
+  int ctas_per_sm; /* resident CTAs per SM, 1..4 (0 = 2) */
+} mgs_tune;
+
+size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, const mgs_tune* tune);
+int ls_solve_dd_batched(double* A_pool, double* b_pool, double* x_pool, const int64_t* a_off, const int64_t* b_off,
+                        const int64_t* x_off, const int32_t* m, const int32_t* n, const int32_t* order, int batch,
+                        int max_m, int max_n, void* workspace, size_t workspace_bytes, int32_t* dev_status,
+                        const mgs_tune* tune, void* stream);
+int ls_solve_qd_batched(double* A_pool, double* b_pool, double* x_pool, const int64_t* a_off, const int64_t* b_off,
+                        const int64_t* x_off, const int32_t* m, const int32_t* n, const int32_t* order, int batch,
+                        int max_m, int max_n, void* workspace, size_t workspace_bytes, int32_t* dev_status,
+                        const mgs_tune* tune, void* stream);
+
+/*
  * ls_solve_dd without a caller workspace, for callers that cannot allocate device memory
  * (a host whose device memory is all owned by another allocator, or an application that
  * must not allocate after start-up).  The paper has no counterpart: it is a packaging of

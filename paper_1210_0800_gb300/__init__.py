@@ -5,7 +5,12 @@ this package only builds it, marshals tensors into it, and generates synthetic i
 """
 
 from ._binding import (  # noqa: F401
+    Batch,
     MGSError,
+    make_batch,
+    ls_solve_batched,
+    ls_solve_dd_batched,
+    ls_solve_qd_batched,
     STATUS_NAMES,
     library_path,
     load,

@@ -17,7 +17,13 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
                 5: "MGS_ECUDA", 6: "MGS_ENOSPACE"}
 
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
-           "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc"]
+           "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
+           "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched"]
+
+
+class MgsTune(ctypes.Structure):
+    """Launch shape of the batched solve (mgs_tune in the C header)."""
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 _lib = None
 
@@ -58,6 +64,12 @@ def load(path: str | None = None):
         getattr(lib, name).argtypes = ls_args
     lib.ls_solve_dd_noalloc.restype = i
     lib.ls_solve_dd_noalloc.argtypes = [dp, i, dp, dp, dp, i, dp, i, i, vp, vp]
+    tp = ctypes.POINTER(MgsTune)
+    lib.mgs_batched_workspace_bytes.restype = sz
+    lib.mgs_batched_workspace_bytes.argtypes = [i, i, i, i, tp]
+    for name in ("ls_solve_dd_batched", "ls_solve_qd_batched"):
+        getattr(lib, name).restype = i
+        getattr(lib, name).argtypes = [dp, dp, dp, vp, vp, vp, vp, vp, vp, i, i, i, vp, sz, vp, tp, vp]
     if path == _build.LIBRARY:
         _lib = lib
     return lib
@@ -188,3 +200,83 @@ def mgs_qr_qd(A, R=None, workspace=None, status=None, stream=None):
 
 def mgs_workspace_bytes(limbs: int, m: int, n: int, with_rhs: bool = True) -> int:
     return workspace_bytes(limbs, m, n, with_rhs)
+
+
+# ----------------------------------------------------------------------------- batched
+
+
+class Batch:
+    """Device pools and index arrays of a ragged batch of least-squares systems.
+
+    A_pool (sum m_i n_i, 2, L), b_pool (sum m_i, 2, L), x_pool (sum n_i, 2, L), element
+    offsets a_off/b_off/x_off (int64), sizes m/n (int32), all on one CUDA device."""
+
+    def __init__(self, A_pool, b_pool, x_pool, a_off, b_off, x_off, m, n, max_m, max_n, order=None):
+        self.A_pool, self.b_pool, self.x_pool = A_pool, b_pool, x_pool
+        self.a_off, self.b_off, self.x_off, self.m, self.n = a_off, b_off, x_off, m, n
+        self.max_m, self.max_n, self.order = max_m, max_n, order
+        self.batch = int(m.numel())
+        self.limbs = int(A_pool.shape[-1])
+
+
+def make_batch(systems, device, largest_first=True):
+    """Pack a list of (A (n, m, 2, L), b (m, 2, L)) numpy systems into a Batch (copies to
+    the device).  largest_first: hand the systems out in decreasing m n^2 order."""
+    import numpy as np
+    import torch
+
+    L = systems[0][0].shape[-1]
+    ms = np.array([A.shape[1] for A, _ in systems], dtype=np.int32)
+    ns = np.array([A.shape[0] for A, _ in systems], dtype=np.int32)
+    a_off = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(ms.astype(np.int64))[:-1]]).astype(np.int64)
+    x_off = np.concatenate([[0], np.cumsum(ns.astype(np.int64))[:-1]]).astype(np.int64)
+    A_pool = np.concatenate([A.reshape(-1, 2, L) for A, _ in systems])
+    b_pool = np.concatenate([b.reshape(-1, 2, L) for _, b in systems])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+    order = None
+    if largest_first:
+        order = t(np.argsort(-(ms.astype(np.float64) * ns.astype(np.float64) ** 2), kind="stable").astype(np.int32))
+    x_pool = torch.zeros((int(ns.sum()), 2, L), dtype=torch.float64, device=device)
+    return Batch(t(A_pool), t(b_pool), x_pool, t(a_off), t(b_off), t(x_off), t(ms), t(ns),
+                 int(ms.max()), int(ns.max()), order)
+
+
+def batched_workspace_bytes(limbs, batch, max_m, max_n, tune=None):
+    tp = ctypes.byref(MgsTune(*tune)) if tune else None
+    return int(load().mgs_batched_workspace_bytes(limbs, batch, max_m, max_n, tp))
+
+
+def ls_solve_batched(bt, workspace=None, status=None, tune=None, stream=None):
+    """Solve every system of Batch `bt` in one launch (A -> Q, b -> residual, x filled).
+    tune = (threads, ctas_per_sm) or None.  Returns the per-system status tensor."""
+    import torch
+
+    L = bt.limbs
+    dev = bt.A_pool.device
+    need = batched_workspace_bytes(L, bt.batch, bt.max_m, bt.max_n, tune)
+    if need == 0:
+        raise MGSError(MGS_ENOSPACE, "unsupported batch shape")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    if status is None:
+        status = torch.empty(bt.batch, dtype=torch.int32, device=dev)
+    fn = load().ls_solve_dd_batched if L == 2 else load().ls_solve_qd_batched
+    tp = ctypes.byref(MgsTune(*tune)) if tune else None
+    rc = fn(_ptr(bt.A_pool), _ptr(bt.b_pool), _ptr(bt.x_pool), _ptr(bt.a_off), _ptr(bt.b_off), _ptr(bt.x_off),
+            _ptr(bt.m), _ptr(bt.n), _ptr(bt.order), bt.batch, bt.max_m, bt.max_n, _ptr(workspace),
+            ctypes.c_size_t(workspace.numel()), _ptr(status), tp, _stream(stream))
+    if rc != MGS_OK:
+        extra = " (cudaError %d)" % load().mgs_last_cuda_error() if rc == MGS_ECUDA else ""
+        raise MGSError(rc, "ls_solve_batched%s" % extra)
+    return status
+
+
+def ls_solve_dd_batched(bt, workspace=None, status=None, tune=None, stream=None):
+    assert bt.limbs == 2
+    return ls_solve_batched(bt, workspace, status, tune, stream)
+
+
+def ls_solve_qd_batched(bt, workspace=None, status=None, tune=None, stream=None):
+    assert bt.limbs == 4
+    return ls_solve_batched(bt, workspace, status, tune, stream)

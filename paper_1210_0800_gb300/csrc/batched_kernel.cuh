@@ -1,0 +1,300 @@
+// Batched least squares: many independent complex DD/QD systems of different sizes in
+// one launch (the pleasingly parallel case the paper sets aside when it tracks a single
+// path, Section 2).  Each system is solved by one CTA with the method of Section 3
+// (MGS on [A b], Figure 1 and Eq. 1) and Section 6 (back substitution, Figure 3).
+//
+// Organisation: CTAs take systems from a device work queue (an atomic counter over an
+// optional order array, e.g. largest first); no CTA ever waits for another.  A system's
+// matrix stays in global memory (L1/L2); the pivot column, the reduction tree and the
+// coefficients are in shared memory.  Per step: Gram partials of all trailing columns
+// against the pivot (one lane per (column, part, row chunk)), a shared-memory tree,
+// c_kj = G_kj / G_kk, the update a_j -= c_kj a_k.  Normalisation and the scaled back
+// substitution follow the single-system kernel.
+#pragma once
+
+#include <cstdint>
+
+#include "ddqd.cuh"
+#include "mgs_kernel.cuh"
+
+namespace mgs {
+
+struct BatchParams {
+  double* A;  // pool; system i at A + a_off[i] * 2L, column-major with leading dimension m_i
+  double* b;  // pool; system i at b + b_off[i] * 2L (m_i elements)
+  double* x;  // pool; system i at x + x_off[i] * 2L (n_i elements)
+  const long long* a_off;
+  const long long* b_off;
+  const long long* x_off;
+  const int* m_arr;
+  const int* n_arr;
+  const int* order;  // optional: the queue hands out order[0], order[1], ... (nullptr: 0, 1, ...)
+  int batch, max_m, max_n;
+  unsigned* counter;  // work-queue head (zeroed before the launch)
+  double* ws;         // per-CTA scratch, per_cta doubles each
+  long long per_cta;
+  int* status;  // one word per system
+  double one, nzero;
+};
+
+// Shared memory of one batched CTA.
+__host__ __device__ inline size_t batched_smem_bytes(int L, int T, int max_m, int max_n) {
+  const size_t E = 2 * (size_t)L;
+  return sizeof(double) * ((size_t)max_m * E          // pivot column
+                           + (size_t)(max_n + 1) * E  // coefficients / Gram row
+                           + (size_t)T * L            // reduction tree
+                           + 2 * E)
+         + 16 * sizeof(int);
+}
+
+// Per-CTA global scratch (doubles): packed upper R (coefficients, then scaled columns),
+// y, G_kk, r_kk, 1/r_kk.
+__host__ __device__ inline long long batched_scratch_doubles(int L, int max_n) {
+  const long long E = 2 * (long long)L, nc = max_n + 1;
+  const long long v = (long long)max_n * (max_n + 1) / 2 * E + nc * E + 3 * nc * L;
+  return (v + 31) / 32 * 32;
+}
+
+template <class Ar, int T>
+__global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
+  constexpr int L = Ar::L, E = 2 * L;
+  using elem = typename Ar::elem;
+  using real = typename Ar::real;
+  using pacc = typename Ar::pacc;
+  constexpr int PACC = Ar::PACC;
+  const Fp f{bp.one, bp.nzero};
+  const int tid = threadIdx.x;
+
+  extern __shared__ __align__(16) double sm[];
+  double* piv = sm;                               // max_m * E, element l at l * E
+  double* gbuf = piv + (size_t)bp.max_m * E;       // (max_n + 1) * E
+  pacc* red = reinterpret_cast<pacc*>(gbuf + (size_t)(bp.max_n + 1) * E);  // T
+  int* sflag = reinterpret_cast<int*>(reinterpret_cast<double*>(red) + (size_t)T * L + 2 * E);
+
+  double* scr = bp.ws + (size_t)blockIdx.x * bp.per_cta;
+  double* Rp = scr;  // packed upper triangle: (k, j), k <= j, at (j (j + 1) / 2 + k) * E
+  double* Yv = Rp + (size_t)bp.max_n * (bp.max_n + 1) / 2 * E;
+  double* Gd = Yv + (size_t)(bp.max_n + 1) * E;
+  double* Rd = Gd + (size_t)(bp.max_n + 1) * L;
+  double* Ri = Rd + (size_t)(bp.max_n + 1) * L;
+
+  auto ld_real = [&](const double* src) {
+    real r;
+    double* d = reinterpret_cast<double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) d[q] = src[q];
+    return r;
+  };
+  auto st_real = [&](double* dst, const real& r) {
+    const double* d = reinterpret_cast<const double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) dst[q] = d[q];
+  };
+  auto ld_part = [&](const double* p, int part) {
+    elem e;
+#pragma unroll
+    for (int q = 0; q < E; ++q) e.v[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) e.v[part * L + q] = p[part * L + q];
+    return e;
+  };
+  auto st_part = [&](double* p, const elem& e, int part) {
+#pragma unroll
+    for (int q = 0; q < L; ++q) p[part * L + q] = e.v[part * L + q];
+  };
+  auto packed = [](int k, int j) { return (size_t)j * (j + 1) / 2 + k; };
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      sflag[0] = (int)atomicAdd(bp.counter, 1u);
+      sflag[1] = ST_OK;
+    }
+    __syncthreads();
+    const int qi = sflag[0];
+    if (qi >= bp.batch) break;
+    const int sys = bp.order ? bp.order[qi] : qi;
+    const int m = bp.m_arr[sys], n = bp.n_arr[sys];
+    if (n < 1 || m < n || m > bp.max_m || n > bp.max_n) {
+      if (tid == 0) bp.status[sys] = ST_EINVAL;
+      continue;
+    }
+    const int nc = n + 1;
+    double* A = bp.A + (size_t)bp.a_off[sys] * E;
+    double* bv = bp.b + (size_t)bp.b_off[sys] * E;
+    double* xv = bp.x + (size_t)bp.x_off[sys] * E;
+    auto col = [&](int j) -> double* { return (j < n) ? A + (size_t)j * m * E : bv; };
+    // non-finite input check
+    {
+      bool bad = false;
+      for (int i = tid; i < m * nc * E; i += T) {
+        const int j = i / (m * E), r = i % (m * E);
+        bad |= !finite64(col(j)[r]);
+      }
+      if (bad) sflag[1] = ST_ENONFINITE;
+    }
+    __syncthreads();
+
+    for (int k = 0; k < nc; ++k) {
+      // pivot column rows
+      for (int i = tid; i < m * E; i += T) piv[i] = col(k)[i];
+      __syncthreads();
+      // Gram row G_kj, j >= k: (column, part, row chunk) items; tree over chunks
+      const int cols = nc - k, pairs = 2 * cols;
+      int C = T / pairs;
+      C = max(1, min(C, m));
+      const int per_round = T / C;
+      for (int base = 0; base < pairs; base += per_round) {
+        const int job = tid / C, ch = tid % C, pi = base + job;
+        const bool act = job < per_round && pi < pairs;
+        const int j = k + (pi >> 1), part = pi & 1;
+        pacc a;
+        Ar::pzero(a);
+        if (act && !(j == k && part == 1)) {
+          const double* cj = col(j);
+          for (int l = ch; l < m; l += C) {
+            elem pe, ce;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+              pe.v[q] = piv[(size_t)l * E + q];
+              ce.v[q] = cj[(size_t)l * E + q];
+            }
+            Ar::mac_part(f, a, pe, ce, part);
+          }
+        }
+        red[tid] = a;
+        __syncthreads();
+        for (int st = 1; st < C; st <<= 1) {
+          if (act && (ch % (2 * st)) == 0 && ch + st < C) {
+            pacc x = red[tid];
+            Ar::pcombine(f, x, red[tid + st]);
+            red[tid] = x;
+          }
+          __syncthreads();
+        }
+        if (act && ch == 0) {
+          double* dst = gbuf + (size_t)(j - k) * E + part * L;
+          if (j == k && part == 1) {
+#pragma unroll
+            for (int q = 0; q < L; ++q) dst[q] = 0.0;
+          } else {
+            Ar::pfinal(f, red[tid], dst);
+          }
+        }
+        __syncthreads();
+      }
+      const real G = ld_real(gbuf);
+      const bool okpiv = Ar::positive(G);
+      if (tid == 0) st_real(Gd + (size_t)k * L, G);
+      if (k == nc - 1) break;  // the right-hand side: keep G (z^2); its column is the residual
+      if (!okpiv && tid == 0) sflag[1] = (sflag[1] == ST_OK) ? ST_ERANK : sflag[1];
+      // coefficients c_kj = G_kj / G_kk (j > k), stored as row k of R (or y_k)
+      const double invG = Ar::inv_lead(G);
+      for (int t = tid; t < 2 * (cols - 1); t += T) {
+        const int j = k + 1 + (t >> 1), part = t & 1;
+        double* g = gbuf + (size_t)(j - k) * E;
+        const elem ge = ld_part(g, part);
+        elem cc = ge;
+        if (okpiv) {
+          Ar::div_real_part(f, cc, ge, G, invG, part);
+        } else {
+#pragma unroll
+          for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
+        }
+        st_part(g, cc, part);
+        st_part((j < n) ? Rp + packed(k, j) * E : Yv + (size_t)k * E, cc, part);
+      }
+      __syncthreads();
+      // update a_j -= c_kj a_k, j > k (one lane per (column, row, part))
+      const int tot = (cols - 1) * m * 2;
+      for (int idx = tid; idx < tot; idx += T) {
+        const int part = idx & 1, rest = idx >> 1;
+        const int j = k + 1 + rest / m, l = rest % m;
+        double* p = col(j) + (size_t)l * E;
+        elem y = ld_part(p, part), cc, pe;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          cc.v[q] = gbuf[(size_t)(j - k) * E + q];
+          pe.v[q] = piv[(size_t)l * E + q];
+        }
+        Ar::update_part(f, y, cc, pe, part);
+        st_part(p, y, part);
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    // r_kk, 1/r_kk
+    for (int k = tid; k < nc; k += T) {
+      const real r = Ar::sqrt(f, ld_real(Gd + (size_t)k * L));
+      st_real(Rd + (size_t)k * L, r);
+      if (Ar::positive(r)) st_real(Ri + (size_t)k * L, Ar::inv_real(f, r));
+    }
+    __syncthreads();
+    // q_j = a_j / r_jj; the last column (b) is the residual and stays
+    for (int idx = tid; idx < n * m * 2; idx += T) {
+      const int part = idx & 1, rest = idx >> 1;
+      const int j = rest / m, l = rest % m;
+      const real r = ld_real(Rd + (size_t)j * L);
+      if (!Ar::positive(r)) continue;
+      double* p = col(j) + (size_t)l * E;
+      const elem a = ld_part(p, part);
+      elem q = a;
+      Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
+      st_part(p, q, part);
+    }
+    // back substitution on the column-scaled system: t_jk = r_jk / r_kk with
+    // r_jk = c_jk r_jj (so t_jk = c_jk r_jj / r_kk), y_k = c_kn r_kk
+    for (int idx = tid; idx < n * (n - 1); idx += T) {
+      const int part = idx & 1;
+      const int pi = idx >> 1;
+      int k = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pi)) * 0.5);
+      while (k * (k - 1) / 2 > pi) --k;
+      while ((k + 1) * k / 2 <= pi) ++k;
+      const int j = pi - k * (k - 1) / 2;  // j < k
+      double* p = Rp + packed(j, k) * E;
+      const elem c = ld_part(p, part);
+      elem t = c;
+      Ar::mul_real_part(f, t, c, ld_real(Rd + (size_t)j * L), part);
+      const elem t2 = t;
+      Ar::mul_real_part(f, t, t2, ld_real(Ri + (size_t)k * L), part);
+      st_part(p, t, part);
+    }
+    for (int idx = tid; idx < 2 * n; idx += T) {
+      const int k = idx >> 1, part = idx & 1;
+      double* p = Yv + (size_t)k * E;
+      const elem c = ld_part(p, part);
+      elem y = c;
+      Ar::mul_real_part(f, y, c, ld_real(Rd + (size_t)k * L), part);
+      st_part(p, y, part);
+    }
+    __syncthreads();
+    for (int k = n - 1; k >= 0; --k) {
+      elem xk;
+#pragma unroll
+      for (int q = 0; q < E; ++q) xk.v[q] = Yv[(size_t)k * E + q];  // x~_k = y_k
+      for (int t = tid; t < 2 * k; t += T) {
+        const int j = t >> 1, part = t & 1;
+        double* p = Yv + (size_t)j * E;
+        elem y = ld_part(p, part), tt;
+#pragma unroll
+        for (int q = 0; q < E; ++q) tt.v[q] = Rp[packed(j, k) * E + q];
+        Ar::update_part(f, y, tt, xk, part);
+        st_part(p, y, part);
+      }
+      __syncthreads();
+    }
+    // x_k = x~_k / r_kk
+    for (int idx = tid; idx < 2 * n; idx += T) {
+      const int k = idx >> 1, part = idx & 1;
+      const elem xt = ld_part(Yv + (size_t)k * E, part);
+      const real r = ld_real(Rd + (size_t)k * L);
+      elem xo = xt;
+      Ar::div_real_part(f, xo, xt, r, Ar::inv_lead(r), part);
+      st_part(xv + (size_t)k * E, xo, part);
+    }
+    __syncthreads();
+    if (tid == 0) bp.status[sys] = sflag[1];
+  }
+}
+
+}  // namespace mgs

@@ -1,0 +1,102 @@
+"""Batched ragged solve vs the oracle, system by system (x, Q, residual), DD and QD;
+per-system statuses; independence of the hand-out order and of the launch shape."""
+
+import numpy as np
+import pytest
+
+from helpers import TOL, rel
+from paper_1210_0800_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def ragged(orc, L, count, seed, n_lo=1, n_hi=40, extra_hi=8):
+    ms, ns = inputs.ragged_shapes(count, seed, n_lo, n_hi, 0, extra_hi)
+    systems = []
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        A, xt, _ = inputs.system(int(m), int(n), L, inputs.system_seed(seed, i))
+        systems.append((A, orc.matvec(A, xt)))
+    return systems
+
+
+def run(systems, tune=None, largest_first=True):
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    bt = mg.make_batch(systems, torch.device("cuda:0"), largest_first=largest_first)
+    st = mg.ls_solve_batched(bt, tune=tune)
+    torch.cuda.synchronize()
+    return bt, st.cpu().numpy()
+
+
+def unpack(bt, i, systems):
+    A, b = systems[i]
+    n, m = A.shape[0], A.shape[1]
+    ao, bo, xo = int(bt.a_off[i]), int(bt.b_off[i]), int(bt.x_off[i])
+    Q = bt.A_pool[ao:ao + m * n].cpu().numpy().reshape(A.shape)
+    r = bt.b_pool[bo:bo + m].cpu().numpy()
+    x = bt.x_pool[xo:xo + n].cpu().numpy()
+    return Q, r, x
+
+
+@pytest.mark.parametrize("L,count,seed", [(2, 48, 61), (4, 16, 62)])
+def test_batched_vs_oracle(orc, L, count, seed):
+    systems = ragged(orc, L, count, seed)
+    bt, st = run(systems)
+    assert (st == 0).all(), st
+    for i, (A, b) in enumerate(systems):
+        Q, r, x = unpack(bt, i, systems)
+        o = orc.ls_solve(A.copy(), b.copy())
+        assert rel(orc, x, o["x"]) <= TOL[L], i
+        assert rel(orc, Q, o["Q"]) <= TOL[L], i
+        d, _ = orc.max_abs_diff(r, o["resid"])
+        assert d <= TOL[L] * max(1.0, orc.max_abs_diff(b, 0 * b)[0]), i
+
+
+def test_batched_shapes_and_order_agree(orc):
+    """Every launch shape and both hand-out orders solve the batch to the same tolerance."""
+    systems = ragged(orc, 2, 24, 63)
+    ref, _ = run(systems, tune=None, largest_first=False)
+    for tune in [(128, 1), (256, 1), (128, 3), (256, 2)]:
+        bt, st = run(systems, tune=tune, largest_first=True)
+        assert (st == 0).all()
+        for i in range(len(systems)):
+            x0 = unpack(ref, i, systems)[2]
+            x1 = unpack(bt, i, systems)[2]
+            assert rel(orc, x1, x0) <= 1e-26, (tune, i)
+
+
+def test_batched_statuses(orc):
+    """A rank-deficient system reports MGS_ERANK and a non-finite one MGS_ENONFINITE;
+    the others are unaffected."""
+    systems = ragged(orc, 2, 6, 64)
+    A, b = systems[2]
+    A = A.copy()
+    A[0] = 0.0
+    systems[2] = (A, b)
+    A4, b4 = systems[4]
+    b4 = b4.copy()
+    b4[0, 0, 0] = np.inf
+    systems[4] = (A4, b4)
+    bt, st = run(systems)
+    assert st[2] == 2 and st[4] == 3
+    for i in (0, 1, 3, 5):
+        assert st[i] == 0
+        o = orc.ls_solve(systems[i][0].copy(), systems[i][1].copy())
+        assert rel(orc, unpack(bt, i, systems)[2], o["x"]) <= TOL[2]
+
+
+def test_autotuner_picks_a_candidate(tmp_path):
+    import torch
+
+    import oracle
+    import paper_1210_0800_gb300 as mg
+    from paper_1210_0800_gb300 import tune
+
+    systems = ragged(oracle.get(), 2, 32, 65, 8, 24)
+    bt = mg.make_batch(systems, torch.device("cuda:0"))
+    best, times = tune.tune_batched(bt, reps=1, cache_path=str(tmp_path / "c.json"))
+    assert tuple(best) in tune.CANDIDATES and len(times) == len(tune.CANDIDATES)
+    again, _ = tune.tune_batched(bt, cache_path=str(tmp_path / "c.json"))
+    assert tuple(again) == tuple(best)
