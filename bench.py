@@ -491,13 +491,90 @@ def run_gpu_batched(args, rank, world):
     return 0
 
 
+DIFF = {"c4_dd_diff_160x128x64": (2, 160, 128, 64)}
+
+
+def run_gpu_diff(args, rank, world):
+    """One step = forward solve of a batch of uniform systems plus the adjoint for
+    L = sum |x|^2 (dL/dx = 2x), through the torch.autograd.Function."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    L, m, n, B = DIFF[args.workload]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    seed = inputs.system_seed(inputs.BASE_SEED + 4, rank)
+    host = [inputs.system(m, n, L, inputs.system_seed(seed, i)) for i in range(B)]
+    A0 = torch.from_numpy(np.stack([h[0] for h in host])).to(dev)
+    b0 = torch.from_numpy(np.stack([h[2] for h in host])).to(dev)
+    As = [A0.clone().requires_grad_(True) for _ in range(K + W)]
+    bs = [b0.clone().requires_grad_(True) for _ in range(K + W)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        x = mg.lstsq(As[i], bs[i])
+        x.backward(gradient=2.0 * x.detach())
+
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0e.record(stream)
+    for i in range(K):
+        step(W + i)
+    t1e.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = t0e.elapsed_time(t1e) / K
+    # forward alone, for reference
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.no_grad():
+        f0.record(stream)
+        for i in range(3):
+            mg.lstsq(A0, b0)
+        f1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = f0.elapsed_time(f1) / 3
+    if rank != 0:
+        return 0
+    ops = B * fp64_ops(L, m, n)
+    peaks = read_peaks()
+    peak_ops = peak_fp64_ops_per_s(float(peaks.get("sm_max_mhz", 2070.0)))
+    line = {
+        "metric": METRIC, "value": world * B / (ms / 1000.0), "unit": "systems/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "systems_per_step": B,
+                   "step": "forward solve + adjoint (dL/dA, dL/db for L = sum |x|^2) via torch.autograd.Function",
+                   "l2": "distinct input copies per step (%.0f MB)" % (A0.numel() * 8 / 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": None,
+        "gpu_launches": 2 * K,
+        "roofline": {"bound": "alu", "achieved": 2 * ops / (ms / 1000.0) / 1e12, "peak": 2 * peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": ops / (ms / 1000.0) / peak_ops, "traffic": None,
+                     "note": "algorithmic FP64 instructions of the forward solves only (%.4g) per step" % ops},
+        "forward_only": {"value": world * B / (fwd_ms / 1000.0), "unit": "systems/s", "ms": fwd_ms},
+        "backward_overhead": (ms - fwd_ms) / fwd_ms,
+    }
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCHED))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(DIFF))
     ap.add_argument("--seq-sample", type=int, default=64, help="systems solved one by one for the comparison")
     ap.add_argument("--ref-seconds", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -508,6 +585,11 @@ def main(argv=None):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    if args.workload in DIFF:
+        if args.impl == "reference":
+            L, m, n, B = DIFF[args.workload]
+            return run_reference(args, L, m, n, rank, world)
+        return run_gpu_diff(args, rank, world)
     if args.workload in BATCHED:
         if args.impl == "reference":
             L, batch, n_rng, e_rng = BATCHED[args.workload]

@@ -120,19 +120,47 @@ int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, do
  * One CTA solves one system at a time; no CTA waits for another.
  */
 typedef struct {
-  int threads;     /* threads per CTA: 128 or 256 (0 = 128) */
-  int ctas_per_sm; /* resident CTAs per SM, 1..4 (0 = 2) */
+  int threads;     /* threads per CTA: 128 or 256 (0 = 256) */
+  int ctas_per_sm; /* resident CTAs per SM, 1..4 (0 = 1) */
 } mgs_tune;
 
 size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, const mgs_tune* tune);
-int ls_solve_dd_batched(double* A_pool, double* b_pool, double* x_pool, const int64_t* a_off, const int64_t* b_off,
-                        const int64_t* x_off, const int32_t* m, const int32_t* n, const int32_t* order, int batch,
-                        int max_m, int max_n, void* workspace, size_t workspace_bytes, int32_t* dev_status,
-                        const mgs_tune* tune, void* stream);
-int ls_solve_qd_batched(double* A_pool, double* b_pool, double* x_pool, const int64_t* a_off, const int64_t* b_off,
-                        const int64_t* x_off, const int32_t* m, const int32_t* n, const int32_t* order, int batch,
-                        int max_m, int max_n, void* workspace, size_t workspace_bytes, int32_t* dev_status,
-                        const mgs_tune* tune, void* stream);
+/* R_pool (optional, may be NULL): packed upper triangle of R of system i at
+ * R_pool + r_off[i]*2L, element (k, j), k <= j, at index j(j+1)/2 + k (n(n+1)/2 elements). */
+int ls_solve_dd_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,
+                        const int64_t* b_off, const int64_t* x_off, const int64_t* r_off, const int32_t* m,
+                        const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                        size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream);
+int ls_solve_qd_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,
+                        const int64_t* b_off, const int64_t* x_off, const int64_t* r_off, const int32_t* m,
+                        const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                        size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream);
+
+/*
+ * Adjoint (backward) of the batched least squares: for a real loss with gradient
+ * G = dL/dRe(x) + i dL/dIm(x) (PyTorch's convention for complex tensors), the gradients
+ * with respect to A and b.  The paper has no backward pass; this differentiates the
+ * solve of Section 3 (Eq. 1) and Section 6 through the normal equations A^H A x = A^H b:
+ *     u = R^{-H} G,  w = R^{-1} u,  grad_b = A w = Q u,  grad_A = r w^H - grad_b x^H,
+ * with Q, R, x and the residual r = b - A x of the forward solve (two triangular solves,
+ * one matrix-vector product, one rank-2 update per system; one CTA per system).
+ *   Q_pool, x_pool, r_pool  the forward's outputs (A_pool, x_pool and b_pool after the solve)
+ *   R_pool, r_off           the forward's packed R (ls_solve_*_batched with R_pool)
+ *   G_pool                  gradient of x, laid out like x_pool
+ *   gA_pool, gb_pool        outputs, laid out like A_pool and b_pool
+ *   workspace               at least 256 bytes (a work-queue counter)
+ *   dev_status              per-system status (MGS_ERANK for a zero r_kk)
+ */
+int ls_adjoint_dd_batched(const double* Q_pool, const double* R_pool, const double* x_pool, const double* r_pool,
+                          const double* G_pool, double* gA_pool, double* gb_pool, const int64_t* a_off,
+                          const int64_t* r_off, const int64_t* b_off, const int64_t* x_off, const int32_t* m,
+                          const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                          size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream);
+int ls_adjoint_qd_batched(const double* Q_pool, const double* R_pool, const double* x_pool, const double* r_pool,
+                          const double* G_pool, double* gA_pool, double* gb_pool, const int64_t* a_off,
+                          const int64_t* r_off, const int64_t* b_off, const int64_t* x_off, const int32_t* m,
+                          const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                          size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream);
 
 /*
  * ls_solve_dd without a caller workspace, for callers that cannot allocate device memory

@@ -77,6 +77,8 @@ class Oracle:
             "oracle_residual": (d, [i, vp, i, vp, vp, i, i, i, vp]),
             "oracle_rinv_fro": (d, [i, vp, i, i]),
             "oracle_max_abs_diff": (d, [i, vp, i, vp, ctypes.c_long, vp]),
+            "oracle_fwdsub_conjT": (i, [i, vp, i, i, vp, vp]),
+            "oracle_ls_adjoint": (i, [i, vp, vp, vp, i, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -207,6 +209,18 @@ class Oracle:
         bmax = ctypes.c_double(0.0)
         d = self.lib.oracle_max_abs_diff(La, _ptr(a), Lb, _ptr(b), ca, ctypes.byref(bmax))
         return float(d), float(bmax.value)
+
+
+    def ls_adjoint(self, A, b, G):
+        """Gradients (grad_A, grad_b) of a real loss with dL/dx = G (PyTorch's complex
+        convention) through x = argmin ||b - A x||; also returns x and the status."""
+        n, m, _, L = A.shape
+        gA = np.zeros_like(A)
+        gb = np.zeros((m, 2, L))
+        x = np.zeros((n, 2, L))
+        st = self.lib.oracle_ls_adjoint(L, _ptr(np.ascontiguousarray(A)), _ptr(np.ascontiguousarray(b)),
+                                        _ptr(np.ascontiguousarray(G)), m, n, _ptr(gA), _ptr(gb), _ptr(x))
+        return gA, gb, x, int(st)
 
 
 _default: Oracle | None = None

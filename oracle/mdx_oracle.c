@@ -778,3 +778,87 @@ EXPORT double oracle_max_abs_diff(int La, const double *a, int Lb, const double 
   if (max_abs_b) *max_abs_b = bmax;
   return dmax;
 }
+
+/* ---------------------------------------------------------------- adjoint of least squares */
+
+/*
+ * Forward substitution with the conjugate transpose: R^H u = g (R upper triangular with
+ * real diagonal), column order: for k = 0..n-1, u_k = g_k / r_kk, then
+ * g_j -= conj(r_kj) u_k for j > k.  g is overwritten.
+ */
+EXPORT int oracle_fwdsub_conjT(int L, const double *R, int ldr, int n, double *g, double *u) {
+  int status = 0;
+  for (int k = 0; k < n; ++k) {
+    mp rkk = cx_load(ELEM(R, k, k, ldr, L), L).re;
+    if (rkk.v[0] == 0.0) status = 2;
+    cx uk = cx_div_real(cx_load(g + (size_t)k * 2 * L, L), rkk, L);
+    cx_store(u + (size_t)k * 2 * L, &uk, L);
+    for (int j = k + 1; j < n; ++j) {
+      cx rkj = cx_load(ELEM(R, k, j, ldr, L), L);
+      cx gj = cx_sub(cx_load(g + (size_t)j * 2 * L, L), cx_conjmul(rkj, uk, L), L);
+      cx_store(g + (size_t)j * 2 * L, &gj, L);
+    }
+  }
+  return status;
+}
+
+/*
+ * Adjoint of x = argmin ||b - A x|| for a real loss L(x) with gradient G = dL/dRe(x) +
+ * i dL/dIm(x): from A^H A x = A^H b,
+ *     w = (A^H A)^{-1} G = R^{-1} R^{-H} G,   grad_b = A w = Q R^{-H} G,
+ *     grad_A = r w^H - grad_b x^H,             r = b - A x,
+ * with Q, R, x, r from MGS on [A b] (Eq. 1) and Figure 3.  Every product of grad_A is
+ * formed exactly and rounded once.  A (m x n) and b are the original inputs.
+ * Returns 0, or the status of the solve.
+ */
+EXPORT int oracle_ls_adjoint(int L, const double *A, const double *b, const double *G, int m, int n, double *gA,
+                             double *gb, double *x_out) {
+  size_t es = 2 * (size_t)L;
+  double *Q = (double *)malloc(sizeof(double) * es * (size_t)m * n);
+  double *r = (double *)malloc(sizeof(double) * es * (size_t)m);
+  double *R = (double *)calloc(es * (size_t)n * n, sizeof(double));
+  double *x = (double *)malloc(sizeof(double) * es * (size_t)n);
+  double *g = (double *)malloc(sizeof(double) * es * (size_t)n);
+  double *u = (double *)malloc(sizeof(double) * es * (size_t)n);
+  double *w = (double *)malloc(sizeof(double) * es * (size_t)n);
+  if (!Q || !r || !R || !x || !g || !u || !w) return 1;
+  memcpy(Q, A, sizeof(double) * es * m * n);
+  memcpy(r, b, sizeof(double) * es * m);
+  int st = oracle_ls_solve(L, Q, r, x, R, NULL, m, n, m, n);
+  memcpy(g, G, sizeof(double) * es * n);
+  st |= oracle_fwdsub_conjT(L, R, n, n, g, u);  /* u = R^{-H} G */
+  memcpy(g, u, sizeof(double) * es * n);
+  st |= oracle_backsub(L, R, n, n, g, w);        /* w = R^{-1} u */
+  oracle_matvec(L, Q, m, n, m, u, L, gb);        /* grad_b = Q u */
+  static __thread xp Er, Ei;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < m; ++i) {
+      cx ri = cx_load(r + (size_t)i * es, L), wj = cx_load(w + (size_t)j * es, L);
+      cx gi = cx_load(gb + (size_t)i * es, L), xj = cx_load(x + (size_t)j * es, L);
+      Er.n = 0;
+      Ei.n = 0;
+      /* r_i conj(w_j) = (rr wr + ri wi) + i (ri wr - rr wi) */
+      xp_add_prod(&Er, &ri.re, &wj.re, L, 1.0);
+      xp_add_prod(&Er, &ri.im, &wj.im, L, 1.0);
+      xp_add_prod(&Ei, &ri.im, &wj.re, L, 1.0);
+      xp_add_prod(&Ei, &ri.re, &wj.im, L, -1.0);
+      /* - g_i conj(x_j) */
+      xp_add_prod(&Er, &gi.re, &xj.re, L, -1.0);
+      xp_add_prod(&Er, &gi.im, &xj.im, L, -1.0);
+      xp_add_prod(&Ei, &gi.im, &xj.re, L, -1.0);
+      xp_add_prod(&Ei, &gi.re, &xj.im, L, 1.0);
+      cx o;
+      o.re = xp_round(&Er, L);
+      o.im = xp_round(&Ei, L);
+      cx_store(ELEM(gA, i, j, m, L), &o, L);
+    }
+  if (x_out) memcpy(x_out, x, sizeof(double) * es * n);
+  free(Q);
+  free(r);
+  free(R);
+  free(x);
+  free(g);
+  free(u);
+  free(w);
+  return st;
+}

@@ -8,6 +8,7 @@ from ._binding import (  # noqa: F401
     Batch,
     MGSError,
     make_batch,
+    ls_adjoint_batched,
     ls_solve_batched,
     ls_solve_dd_batched,
     ls_solve_qd_batched,
@@ -21,3 +22,4 @@ from ._binding import (  # noqa: F401
     mgs_qr_qd,
     mgs_workspace_bytes,
 )
+from .autograd import LeastSquares, lstsq  # noqa: F401,E402

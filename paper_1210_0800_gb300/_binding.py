@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
 
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
-           "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched"]
+           "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
+           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched"]
 
 
 class MgsTune(ctypes.Structure):
@@ -69,7 +70,11 @@ def load(path: str | None = None):
     lib.mgs_batched_workspace_bytes.argtypes = [i, i, i, i, tp]
     for name in ("ls_solve_dd_batched", "ls_solve_qd_batched"):
         getattr(lib, name).restype = i
-        getattr(lib, name).argtypes = [dp, dp, dp, vp, vp, vp, vp, vp, vp, i, i, i, vp, sz, vp, tp, vp]
+        getattr(lib, name).argtypes = [dp, dp, dp, dp, vp, vp, vp, vp, vp, vp, vp, i, i, i, vp, sz, vp, tp, vp]
+    for name in ("ls_adjoint_dd_batched", "ls_adjoint_qd_batched"):
+        getattr(lib, name).restype = i
+        getattr(lib, name).argtypes = [dp, dp, dp, dp, dp, dp, dp, vp, vp, vp, vp, vp, vp, vp, i, i, i, vp, sz, vp,
+                                       tp, vp]
     if path == _build.LIBRARY:
         _lib = lib
     return lib
@@ -211,12 +216,25 @@ class Batch:
     A_pool (sum m_i n_i, 2, L), b_pool (sum m_i, 2, L), x_pool (sum n_i, 2, L), element
     offsets a_off/b_off/x_off (int64), sizes m/n (int32), all on one CUDA device."""
 
-    def __init__(self, A_pool, b_pool, x_pool, a_off, b_off, x_off, m, n, max_m, max_n, order=None):
+    def __init__(self, A_pool, b_pool, x_pool, a_off, b_off, x_off, m, n, max_m, max_n, order=None, R_pool=None,
+                 r_off=None):
         self.A_pool, self.b_pool, self.x_pool = A_pool, b_pool, x_pool
         self.a_off, self.b_off, self.x_off, self.m, self.n = a_off, b_off, x_off, m, n
         self.max_m, self.max_n, self.order = max_m, max_n, order
+        self.R_pool, self.r_off = R_pool, r_off  # optional packed-R output
         self.batch = int(m.numel())
         self.limbs = int(A_pool.shape[-1])
+
+    def with_R(self):
+        """Allocate the packed-R output pool (n(n+1)/2 elements per system)."""
+        import torch
+
+        ns = self.n.to(torch.int64)
+        sizes = ns * (ns + 1) // 2
+        self.r_off = torch.cumsum(sizes, 0) - sizes
+        self.R_pool = torch.zeros((int(sizes.sum().item()), 2, self.limbs), dtype=torch.float64,
+                                  device=self.A_pool.device)
+        return self
 
 
 def make_batch(systems, device, largest_first=True):
@@ -263,9 +281,9 @@ def ls_solve_batched(bt, workspace=None, status=None, tune=None, stream=None):
         status = torch.empty(bt.batch, dtype=torch.int32, device=dev)
     fn = load().ls_solve_dd_batched if L == 2 else load().ls_solve_qd_batched
     tp = ctypes.byref(MgsTune(*tune)) if tune else None
-    rc = fn(_ptr(bt.A_pool), _ptr(bt.b_pool), _ptr(bt.x_pool), _ptr(bt.a_off), _ptr(bt.b_off), _ptr(bt.x_off),
-            _ptr(bt.m), _ptr(bt.n), _ptr(bt.order), bt.batch, bt.max_m, bt.max_n, _ptr(workspace),
-            ctypes.c_size_t(workspace.numel()), _ptr(status), tp, _stream(stream))
+    rc = fn(_ptr(bt.A_pool), _ptr(bt.b_pool), _ptr(bt.x_pool), _ptr(bt.R_pool), _ptr(bt.a_off), _ptr(bt.b_off),
+            _ptr(bt.x_off), _ptr(bt.r_off), _ptr(bt.m), _ptr(bt.n), _ptr(bt.order), bt.batch, bt.max_m, bt.max_n,
+            _ptr(workspace), ctypes.c_size_t(workspace.numel()), _ptr(status), tp, _stream(stream))
     if rc != MGS_OK:
         extra = " (cudaError %d)" % load().mgs_last_cuda_error() if rc == MGS_ECUDA else ""
         raise MGSError(rc, "ls_solve_batched%s" % extra)
@@ -280,3 +298,32 @@ def ls_solve_dd_batched(bt, workspace=None, status=None, tune=None, stream=None)
 def ls_solve_qd_batched(bt, workspace=None, status=None, tune=None, stream=None):
     assert bt.limbs == 4
     return ls_solve_batched(bt, workspace, status, tune, stream)
+
+
+def ls_adjoint_batched(bt, G_pool, gA_pool=None, gb_pool=None, workspace=None, status=None, tune=None, stream=None):
+    """Gradients of a real loss through the batched solve already run on `bt` (which must
+    hold Q in A_pool, the residual in b_pool, x in x_pool and the packed R).  G_pool is
+    dL/dx laid out like x_pool.  Returns (gA_pool, gb_pool, status)."""
+    import torch
+
+    if bt.R_pool is None:
+        raise ValueError("the forward solve must have produced R (Batch.with_R())")
+    dev = bt.A_pool.device
+    if gA_pool is None:
+        gA_pool = torch.empty_like(bt.A_pool)
+    if gb_pool is None:
+        gb_pool = torch.empty_like(bt.b_pool)
+    if workspace is None:
+        workspace = torch.empty(256, dtype=torch.uint8, device=dev)
+    if status is None:
+        status = torch.empty(bt.batch, dtype=torch.int32, device=dev)
+    fn = load().ls_adjoint_dd_batched if bt.limbs == 2 else load().ls_adjoint_qd_batched
+    tp = ctypes.byref(MgsTune(*tune)) if tune else None
+    rc = fn(_ptr(bt.A_pool), _ptr(bt.R_pool), _ptr(bt.x_pool), _ptr(bt.b_pool), _ptr(G_pool), _ptr(gA_pool),
+            _ptr(gb_pool), _ptr(bt.a_off), _ptr(bt.r_off), _ptr(bt.b_off), _ptr(bt.x_off), _ptr(bt.m), _ptr(bt.n),
+            _ptr(bt.order), bt.batch, bt.max_m, bt.max_n, _ptr(workspace), ctypes.c_size_t(workspace.numel()),
+            _ptr(status), tp, _stream(stream))
+    if rc != MGS_OK:
+        extra = " (cudaError %d)" % load().mgs_last_cuda_error() if rc == MGS_ECUDA else ""
+        raise MGSError(rc, "ls_adjoint_batched%s" % extra)
+    return gA_pool, gb_pool, status

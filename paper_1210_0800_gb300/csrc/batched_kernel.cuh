@@ -29,6 +29,8 @@ struct BatchParams {
   const int* m_arr;
   const int* n_arr;
   const int* order;  // optional: the queue hands out order[0], order[1], ... (nullptr: 0, 1, ...)
+  double* R;         // optional output: packed upper triangle of R, system i at R + r_off[i] * 2L
+  const long long* r_off;
   int batch, max_m, max_n;
   unsigned* counter;  // work-queue head (zeroed before the launch)
   double* ws;         // per-CTA scratch, per_cta doubles each
@@ -242,6 +244,27 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
       Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
       st_part(p, q, part);
     }
+    // optional R output (packed upper triangle): r_kj = c_kj r_kk, real diagonal r_jj
+    if (bp.R) {
+      double* Ro = bp.R + (size_t)bp.r_off[sys] * E;
+      for (int idx = tid; idx < n * (n + 1); idx += T) {
+        const int part = idx & 1, pi = idx >> 1;
+        int j = (int)((sqrt(1.0 + 8.0 * (double)pi) - 1.0) * 0.5);  // pi = j (j + 1) / 2 + k
+        while (j * (j + 1) / 2 > pi) --j;
+        while ((j + 1) * (j + 2) / 2 <= pi) ++j;
+        const int k = pi - j * (j + 1) / 2;
+        elem out;
+        if (k == j) {
+          out = Ar::from_real(ld_real(Rd + (size_t)j * L));
+        } else {
+          const elem c = ld_part(Rp + packed(k, j) * E, part);
+          out = c;
+          Ar::mul_real_part(f, out, c, ld_real(Rd + (size_t)k * L), part);
+        }
+        st_part(Ro + packed(k, j) * E, out, part);
+      }
+      __syncthreads();
+    }
     // back substitution on the column-scaled system: t_jk = r_jk / r_kk with
     // r_jk = c_jk r_jj (so t_jk = c_jk r_jj / r_kk), y_k = c_kn r_kk
     for (int idx = tid; idx < n * (n - 1); idx += T) {
@@ -294,6 +317,176 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
     }
     __syncthreads();
     if (tid == 0) bp.status[sys] = sflag[1];
+  }
+}
+
+}  // namespace mgs
+
+namespace mgs {
+
+// Adjoint of batched least squares (see include/mgs_ddqd.h): per system, from the
+// forward's Q, packed R, x and residual r and the incoming gradient G of x,
+//   u = R^{-H} G, w = R^{-1} u, grad_b = Q u, grad_A = r w^H - grad_b x^H.
+struct AdjParams {
+  const double* Q;   // pool, as A of the forward
+  const double* R;   // packed upper R pool
+  const double* x;   // pool
+  const double* r;   // residual pool (b of the forward after the solve)
+  const double* G;   // gradient of x, pool like x
+  double* gA;        // output, pool like A
+  double* gb;        // output, pool like b
+  const long long* a_off;
+  const long long* r_off;
+  const long long* b_off;
+  const long long* x_off;
+  const int* m_arr;
+  const int* n_arr;
+  const int* order;
+  int batch, max_m, max_n;
+  unsigned* counter;
+  int* status;
+  double one, nzero;
+};
+
+__host__ __device__ inline size_t adjoint_smem_bytes(int L, int max_n) {
+  return sizeof(double) * (3 * (size_t)max_n * 2 * L + 2 * 2 * L) + 16 * sizeof(int);
+}
+
+template <class Ar, int T>
+__global__ void __launch_bounds__(T) mgs_adjoint_kernel(AdjParams ap) {
+  constexpr int L = Ar::L, E = 2 * L;
+  using elem = typename Ar::elem;
+  using real = typename Ar::real;
+  using pacc = typename Ar::pacc;
+  const Fp f{ap.one, ap.nzero};
+  const int tid = threadIdx.x;
+  extern __shared__ __align__(16) double sm[];
+  double* gv = sm;                           // max_n * E: G, reduced in place
+  double* uv = gv + (size_t)ap.max_n * E;    // max_n * E: u = R^{-H} G (kept)
+  double* wv = uv + (size_t)ap.max_n * E;    // max_n * E: u reduced in place, then w
+  int* sflag = reinterpret_cast<int*>(wv + (size_t)ap.max_n * E + 2 * E);
+
+  auto ld_part = [&](const double* p, int part) {
+    elem e;
+#pragma unroll
+    for (int q = 0; q < E; ++q) e.v[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) e.v[part * L + q] = p[part * L + q];
+    return e;
+  };
+  auto st_part = [&](double* p, const elem& e, int part) {
+#pragma unroll
+    for (int q = 0; q < L; ++q) p[part * L + q] = e.v[part * L + q];
+  };
+  auto ld_elem = [&](const double* p) {
+    elem e;
+#pragma unroll
+    for (int q = 0; q < E; ++q) e.v[q] = p[q];
+    return e;
+  };
+  auto packed = [](int k, int j) { return (size_t)j * (j + 1) / 2 + k; };
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      sflag[0] = (int)atomicAdd(ap.counter, 1u);
+      sflag[1] = ST_OK;
+    }
+    __syncthreads();
+    const int qi = sflag[0];
+    if (qi >= ap.batch) break;
+    const int sys = ap.order ? ap.order[qi] : qi;
+    const int m = ap.m_arr[sys], n = ap.n_arr[sys];
+    if (n < 1 || m < n || m > ap.max_m || n > ap.max_n) {
+      if (tid == 0) ap.status[sys] = ST_EINVAL;
+      continue;
+    }
+    const double* Q = ap.Q + (size_t)ap.a_off[sys] * E;
+    const double* R = ap.R + (size_t)ap.r_off[sys] * E;
+    const double* xv = ap.x + (size_t)ap.x_off[sys] * E;
+    const double* rv = ap.r + (size_t)ap.b_off[sys] * E;
+    const double* Gv = ap.G + (size_t)ap.x_off[sys] * E;
+    double* gA = ap.gA + (size_t)ap.a_off[sys] * E;
+    double* gb = ap.gb + (size_t)ap.b_off[sys] * E;
+    auto rdiag = [&](int k) {
+      real r;
+      double* d = reinterpret_cast<double*>(&r);
+#pragma unroll
+      for (int q = 0; q < L; ++q) d[q] = R[packed(k, k) * E + q];
+      return r;
+    };
+    for (int i = tid; i < n * E; i += T) gv[i] = Gv[i];
+    __syncthreads();
+    // u = R^{-H} G: for k = 0..n-1, u_k = g_k / r_kk, then g_j -= conj(r_kj) u_k (j > k)
+    for (int k = 0; k < n; ++k) {
+      const real rk = rdiag(k);
+      if (!Ar::positive(rk)) {
+        if (tid == 0) sflag[1] = ST_ERANK;
+      }
+      if (tid < 2) {
+        const elem g = ld_part(gv + (size_t)k * E, tid);
+        elem u = g;
+        Ar::div_real_part(f, u, g, rk, Ar::inv_lead(rk), tid);
+        st_part(uv + (size_t)k * E, u, tid);
+        st_part(wv + (size_t)k * E, u, tid);
+      }
+      __syncthreads();
+      const elem uk = ld_elem(uv + (size_t)k * E);
+      for (int t = tid; t < 2 * (n - 1 - k); t += T) {
+        const int j = k + 1 + (t >> 1), part = t & 1;
+        elem c = ld_elem(R + packed(k, j) * E);
+#pragma unroll
+        for (int q = 0; q < L; ++q) c.v[L + q] = flip_if(c.v[L + q], true);  // conj(r_kj)
+        elem g = ld_part(gv + (size_t)j * E, part);
+        Ar::update_part(f, g, c, uk, part);
+        st_part(gv + (size_t)j * E, g, part);
+      }
+      __syncthreads();
+    }
+    // w = R^{-1} u: for k = n-1..0, w_k = u_k / r_kk, then u_j -= r_jk w_k (j < k);
+    // wv holds u and is reduced in place, w_k replacing u_k
+    for (int k = n - 1; k >= 0; --k) {
+      const real rk = rdiag(k);
+      if (tid < 2) {
+        const elem y = ld_part(wv + (size_t)k * E, tid);
+        elem w = y;
+        Ar::div_real_part(f, w, y, rk, Ar::inv_lead(rk), tid);
+        st_part(wv + (size_t)k * E, w, tid);
+      }
+      __syncthreads();
+      const elem wk = ld_elem(wv + (size_t)k * E);
+      for (int t = tid; t < 2 * k; t += T) {
+        const int j = t >> 1, part = t & 1;
+        elem y = ld_part(wv + (size_t)j * E, part);
+        Ar::update_part(f, y, ld_elem(R + packed(j, k) * E), wk, part);
+        st_part(wv + (size_t)j * E, y, part);
+      }
+      __syncthreads();
+    }
+    // grad_b = Q u: one lane per (row, part)
+    for (int t = tid; t < 2 * m; t += T) {
+      const int i = t >> 1, part = t & 1;
+      pacc a;
+      Ar::pzero(a);
+      for (int k = 0; k < n; ++k) Ar::mul_acc_part(f, a, ld_elem(Q + ((size_t)k * m + i) * E), ld_elem(uv + (size_t)k * E), part);
+      Ar::pfinal(f, a, gb + (size_t)i * E + part * L);
+    }
+    __syncthreads();
+    // grad_A = r w^H - grad_b x^H, element (i, j): r_i conj(w_j) - g_i conj(x_j)
+    for (int t = tid; t < 2 * m * n; t += T) {
+      const int part = t & 1, rest = t >> 1;
+      const int j = rest / m, i = rest % m;
+      elem xn = ld_elem(xv + (size_t)j * E);
+#pragma unroll
+      for (int q = 0; q < E; ++q) xn.v[q] = flip_if(xn.v[q], true);
+      pacc a;
+      Ar::pzero(a);
+      Ar::mac_part(f, a, ld_elem(wv + (size_t)j * E), ld_elem(rv + (size_t)i * E), part);
+      Ar::mac_part(f, a, xn, ld_elem(gb + (size_t)i * E), part);
+      Ar::pfinal(f, a, gA + ((size_t)j * m + i) * E + part * L);
+    }
+    __syncthreads();
+    if (tid == 0) ap.status[sys] = sflag[1];
   }
 }
 
