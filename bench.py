@@ -45,6 +45,9 @@ WORKLOADS = {
     "qd_128": (4, 128, 128, False),
     "qd_256": (4, 256, 256, False),
     "qd_512": (4, 512, 512, False),
+    "d_32": (1, 32, 32, False),
+    "d_128": (1, 128, 128, False),
+    "d_256": (1, 256, 256, False),
 }
 DEFAULT = "c1_qd_320x256"
 # batched workloads: name -> (limbs, batch, n range, extra rows range)
@@ -57,6 +60,7 @@ BATCHED = {
 # complex conjugated multiply-accumulate, complex update y -= c x, |x|^2 accumulate,
 # complex / real division.
 COST = {
+    1: dict(mac=4, upd=4, norm=2, div=2),
     2: dict(mac=36, upd=42, norm=18, div=22),
     4: dict(mac=280, upd=322, norm=140, div=608),
 }
@@ -224,7 +228,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    fn = mg.ls_solve_dd if L == 2 else mg.ls_solve_qd
+    fn = {1: mg.ls_solve_d, 2: mg.ls_solve_dd, 4: mg.ls_solve_qd}[L]
     K, W = args.steps, args.warmup
     total = K + W
     # distinct systems for every step (rank-dependent seeds: replicas solve different systems)
@@ -426,7 +430,7 @@ def run_gpu_batched(args, rank, world):
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / Ke
     # the same systems solved one after another with the single-system solve
-    fn = mg.ls_solve_dd if L == 2 else mg.ls_solve_qd
+    fn = {1: mg.ls_solve_d, 2: mg.ls_solve_dd, 4: mg.ls_solve_qd}[L]
     nseq = min(batch, args.seq_sample)
     sel = list(range(0, batch, max(1, batch // nseq)))[:nseq]
     Ad = [torch.from_numpy(host[i][0]).to(dev) for i in sel]

@@ -58,7 +58,7 @@ int mgs_last_cuda_error(void);
 
 /*
  * Bytes of workspace a call needs on the current device.
- *   limbs    2 (DD) or 4 (QD)
+ *   limbs    1 (complex double), 2 (DD) or 4 (QD)
  *   m, n     matrix size (m >= n >= 1)
  *   with_rhs 1 for ls_solve_* (augmented [A b]), 0 for mgs_qr_*
  * Returns 0 for unsupported arguments or sizes.
@@ -81,6 +81,16 @@ int mgs_qr_dd(double* A, int lda, double* R, int ldr, int m, int n, void* worksp
               int32_t* dev_status, void* stream);
 int mgs_qr_qd(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,
               int32_t* dev_status, void* stream);
+
+/*
+ * Complex double (L = 1: one FP64 number per real part, element = {re, im}) versions of
+ * mgs_qr_* and ls_solve_*: the paper's "complex double" runs (Sections 4 and 8, Tables 2-4),
+ * same method, plain IEEE double arithmetic.  Arguments as for the DD versions.
+ */
+int mgs_qr_d(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,
+             int32_t* dev_status, void* stream);
+int ls_solve_d(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n, void* workspace,
+               size_t workspace_bytes, int32_t* dev_status, void* stream);
 
 /*
  * Least squares: x minimising ||b - A x||_2 (Section 3): modified Gram-Schmidt on the
@@ -127,6 +137,10 @@ typedef struct {
 size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, const mgs_tune* tune);
 /* R_pool (optional, may be NULL): packed upper triangle of R of system i at
  * R_pool + r_off[i]*2L, element (k, j), k <= j, at index j(j+1)/2 + k (n(n+1)/2 elements). */
+int ls_solve_d_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,
+                       const int64_t* b_off, const int64_t* x_off, const int64_t* r_off, const int32_t* m,
+                       const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                       size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream);
 int ls_solve_dd_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,
                         const int64_t* b_off, const int64_t* x_off, const int64_t* r_off, const int32_t* m,
                         const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,

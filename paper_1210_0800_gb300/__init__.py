@@ -15,9 +15,11 @@ from ._binding import (  # noqa: F401
     STATUS_NAMES,
     library_path,
     load,
+    ls_solve_d,
     ls_solve_dd,
     ls_solve_dd_noalloc,
     ls_solve_qd,
+    mgs_qr_d,
     mgs_qr_dd,
     mgs_qr_qd,
     mgs_workspace_bytes,

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
            "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
-           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched"]
+           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched"]
 
 
 class MgsTune(ctypes.Structure):
@@ -57,10 +57,10 @@ def load(path: str | None = None):
     lib.mgs_workspace_bytes.argtypes = [i, i, i, i]
     qr_args = [dp, i, dp, i, i, i, vp, sz, vp, vp]
     ls_args = [dp, i, dp, dp, dp, i, dp, i, i, vp, sz, vp, vp]
-    for name in ("mgs_qr_dd", "mgs_qr_qd"):
+    for name in ("mgs_qr_d", "mgs_qr_dd", "mgs_qr_qd"):
         getattr(lib, name).restype = i
         getattr(lib, name).argtypes = qr_args
-    for name in ("ls_solve_dd", "ls_solve_qd"):
+    for name in ("ls_solve_d", "ls_solve_dd", "ls_solve_qd"):
         getattr(lib, name).restype = i
         getattr(lib, name).argtypes = ls_args
     lib.ls_solve_dd_noalloc.restype = i
@@ -68,7 +68,7 @@ def load(path: str | None = None):
     tp = ctypes.POINTER(MgsTune)
     lib.mgs_batched_workspace_bytes.restype = sz
     lib.mgs_batched_workspace_bytes.argtypes = [i, i, i, i, tp]
-    for name in ("ls_solve_dd_batched", "ls_solve_qd_batched"):
+    for name in ("ls_solve_d_batched", "ls_solve_dd_batched", "ls_solve_qd_batched"):
         getattr(lib, name).restype = i
         getattr(lib, name).argtypes = [dp, dp, dp, dp, vp, vp, vp, vp, vp, vp, vp, i, i, i, vp, sz, vp, tp, vp]
     for name in ("ls_adjoint_dd_batched", "ls_adjoint_qd_batched"):
@@ -131,7 +131,7 @@ def _ls_solve(limbs, A, b, x=None, R=None, z=None, workspace=None, status=None, 
     if status is None:
         status = torch.empty(1, dtype=torch.int32, device=A.device)
     ws, need = _workspace(limbs, m, n, True, A.device, workspace)
-    fn = load().ls_solve_dd if limbs == 2 else load().ls_solve_qd
+    fn = {1: load().ls_solve_d, 2: load().ls_solve_dd, 4: load().ls_solve_qd}[limbs]
     rc = fn(_ptr(A), m, _ptr(b), _ptr(x), _ptr(R), n, _ptr(z), m, n, _ptr(ws), ctypes.c_size_t(ws.numel()),
             _ptr(status), _stream(stream))
     if rc != MGS_OK:
@@ -151,12 +151,22 @@ def _mgs_qr(limbs, A, R=None, workspace=None, status=None, stream=None):
     if status is None:
         status = torch.empty(1, dtype=torch.int32, device=A.device)
     ws, need = _workspace(limbs, m, n, False, A.device, workspace)
-    fn = load().mgs_qr_dd if limbs == 2 else load().mgs_qr_qd
+    fn = {1: load().mgs_qr_d, 2: load().mgs_qr_dd, 4: load().mgs_qr_qd}[limbs]
     rc = fn(_ptr(A), m, _ptr(R), n, m, n, _ptr(ws), ctypes.c_size_t(ws.numel()), _ptr(status), _stream(stream))
     if rc != MGS_OK:
         extra = " (cudaError %d)" % load().mgs_last_cuda_error() if rc == MGS_ECUDA else ""
         raise MGSError(rc, "mgs_qr%s" % extra)
     return R, status
+
+
+def ls_solve_d(A, b, x=None, R=None, z=None, workspace=None, status=None, stream=None):
+    """Complex double least squares (the paper's plain complex double runs)."""
+    return _ls_solve(1, A, b, x, R, z, workspace, status, stream)
+
+
+def mgs_qr_d(A, R=None, workspace=None, status=None, stream=None):
+    """Complex double modified Gram-Schmidt QR; A -> Q in place, returns (R, status)."""
+    return _mgs_qr(1, A, R, workspace, status, stream)
 
 
 def ls_solve_dd(A, b, x=None, R=None, z=None, workspace=None, status=None, stream=None):
@@ -279,7 +289,7 @@ def ls_solve_batched(bt, workspace=None, status=None, tune=None, stream=None):
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     if status is None:
         status = torch.empty(bt.batch, dtype=torch.int32, device=dev)
-    fn = load().ls_solve_dd_batched if L == 2 else load().ls_solve_qd_batched
+    fn = {1: load().ls_solve_d_batched, 2: load().ls_solve_dd_batched, 4: load().ls_solve_qd_batched}[L]
     tp = ctypes.byref(MgsTune(*tune)) if tune else None
     rc = fn(_ptr(bt.A_pool), _ptr(bt.b_pool), _ptr(bt.x_pool), _ptr(bt.R_pool), _ptr(bt.a_off), _ptr(bt.b_off),
             _ptr(bt.x_off), _ptr(bt.r_off), _ptr(bt.m), _ptr(bt.n), _ptr(bt.order), bt.batch, bt.max_m, bt.max_n,

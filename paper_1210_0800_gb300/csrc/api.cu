@@ -34,7 +34,7 @@ int device_sms() {
 
 // Rows per CTA about 64; as many column groups as SMs allow; every row block non-empty.
 bool make_plan(int L, int m, int n, int aug, Plan& pl) {
-  if ((L != 2 && L != 4) || n < 1 || m < n) return false;
+  if ((L != 1 && L != 2 && L != 4) || n < 1 || m < n) return false;
   const int sms = device_sms();
   if (sms <= 0) return false;
   pl.L = L;
@@ -71,7 +71,7 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   pl.off_flags = off;
   off = align256(off + sizeof(int) * (size_t)(pl.nc + 1) * pl.Br);
   pl.zero_bytes = off;
-  const int ACC = (L == 2) ? mgs::DD::ACC : mgs::QD::ACC;
+  const int ACC = (L == 1) ? mgs::D::ACC : (L == 2) ? mgs::DD::ACC : mgs::QD::ACC;
   pl.off_P = off;
   off = align256(off + sizeof(double) * 2 * (size_t)pl.Br * pl.nc * ACC);
   pl.off_V = off;
@@ -147,7 +147,9 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.trace = nullptr;
 #endif
   const int grid = pl.Br * pl.Bc;
-  const int rc = (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st) : mgs::launch_qd(pr, grid, pl.smem, st);
+  const int rc = (L == 1)   ? mgs::launch_d(pr, grid, pl.smem, st)
+                 : (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st)
+                            : mgs::launch_qd(pr, grid, pl.smem, st);
   if (rc != 0) {
     g_last_cuda = rc;
     return MGS_ECUDA;
@@ -199,6 +201,16 @@ size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs) {
   Plan pl;
   if (!make_plan(limbs, m, n, with_rhs, pl)) return 0;
   return pl.total;
+}
+
+int mgs_qr_d(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,
+             int32_t* dev_status, void* stream) {
+  return run(1, A, lda, nullptr, nullptr, R, ldr, nullptr, m, n, workspace, workspace_bytes, dev_status, stream, 0);
+}
+
+int ls_solve_d(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n, void* workspace,
+               size_t workspace_bytes, int32_t* dev_status, void* stream) {
+  return run(1, A, lda, b, x, R, ldr, z, m, n, workspace, workspace_bytes, dev_status, stream, 1);
 }
 
 int mgs_qr_dd(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,

@@ -19,7 +19,7 @@ struct BPlan {
 };
 
 bool make_bplan(int L, int batch, int max_m, int max_n, const mgs_tune* tune, BPlan& bp) {
-  if ((L != 2 && L != 4) || batch < 1 || max_n < 1 || max_m < max_n) return false;
+  if ((L != 1 && L != 2 && L != 4) || batch < 1 || max_n < 1 || max_m < max_n) return false;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
@@ -94,7 +94,9 @@ int run_batched(int L, double* A, double* b, double* x, double* R, const int64_t
   p.one = 1.0;
   p.nzero = -0.0;
   int rc;
-  if (L == 2)
+  if (L == 1)
+    rc = (pl.T == 128) ? launch_batched<mgs::D, 128>(p, pl, st) : launch_batched<mgs::D, 256>(p, pl, st);
+  else if (L == 2)
     rc = (pl.T == 128) ? launch_batched<mgs::DD, 128>(p, pl, st) : launch_batched<mgs::DD, 256>(p, pl, st);
   else
     rc = (pl.T == 128) ? launch_batched<mgs::QD, 128>(p, pl, st) : launch_batched<mgs::QD, 256>(p, pl, st);
@@ -184,6 +186,14 @@ size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, c
   BPlan pl;
   if (!make_bplan(limbs, batch, max_m, max_n, tune, pl)) return 0;
   return pl.total;
+}
+
+int ls_solve_d_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,
+                       const int64_t* b_off, const int64_t* x_off, const int64_t* r_off, const int32_t* m,
+                       const int32_t* n, const int32_t* order, int batch, int max_m, int max_n, void* workspace,
+                       size_t workspace_bytes, int32_t* dev_status, const mgs_tune* tune, void* stream) {
+  return run_batched(1, A_pool, b_pool, x_pool, R_pool, a_off, b_off, x_off, r_off, m, n, order, batch, max_m, max_n,
+                     workspace, workspace_bytes, dev_status, tune, stream);
 }
 
 int ls_solve_dd_batched(double* A_pool, double* b_pool, double* x_pool, double* R_pool, const int64_t* a_off,

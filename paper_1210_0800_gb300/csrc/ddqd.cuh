@@ -112,6 +112,82 @@ __host__ __device__ __forceinline__ bool finite64(double a) {
 }
 
 // =====================================================================================
+// Complex double (one limb): the plain FP64 arithmetic of the paper's "complex double"
+// runs (Sections 4 and 8), with the same interface as DD and QD.
+// =====================================================================================
+struct D {
+  static constexpr int L = 1;
+  static constexpr int ACC = 2;
+  struct real {
+    double h;
+  };
+  struct elem {
+    double v[2];  // re, im
+  };
+  struct acc {
+    double r, i;
+  };
+  struct pacc {
+    double s;
+  };
+  static constexpr int PACC = 1;
+  __host__ __device__ static __forceinline__ void pzero(pacc& a) { a.s = 0.0; }
+  // part 0: a += xr yr + xi yi;  part 1: a += xr yi - xi yr
+  __host__ __device__ static __forceinline__ void mac_part(const Fp& f, pacc& a, const elem& x, const elem& y,
+                                                          int part) {
+    const bool im = part != 0;
+    a.s = f.fma(x.v[0], im ? y.v[1] : y.v[0], a.s);
+    a.s = f.fma(flip_if(x.v[1], im), im ? y.v[0] : y.v[1], a.s);
+  }
+  // part 0: a += rr xr - ri xi;  part 1: a += rr xi + ri xr
+  __host__ __device__ static __forceinline__ void mul_acc_part(const Fp& f, pacc& a, const elem& r, const elem& x,
+                                                              int part) {
+    const bool im = part != 0;
+    a.s = f.fma(r.v[0], im ? x.v[1] : x.v[0], a.s);
+    a.s = f.fma(flip_if(r.v[1], !im), im ? x.v[0] : x.v[1], a.s);
+  }
+  __host__ __device__ static __forceinline__ void pcombine(const Fp& f, pacc& a, const pacc& b) {
+    a.s = f.add(a.s, b.s);
+  }
+  __host__ __device__ static __forceinline__ void pfinal(const Fp&, const pacc& a, double* o) { o[0] = a.s; }
+  __host__ __device__ static __forceinline__ void psub(const Fp& f, double* y, const pacc& a) {
+    y[0] = f.sub(y[0], a.s);
+  }
+  __host__ __device__ static __forceinline__ real re(const elem& x) { return real{x.v[0]}; }
+  // one part of y := y - c x
+  __host__ __device__ static __forceinline__ void update_part(const Fp& f, elem& y, const elem& c, const elem& x,
+                                                             int part) {
+    const bool im = part != 0;
+    double t = im ? y.v[1] : y.v[0];
+    t = f.fma(-c.v[0], im ? x.v[1] : x.v[0], t);
+    t = f.fma(flip_if(c.v[1], im), im ? x.v[0] : x.v[1], t);
+    y.v[0] = im ? y.v[0] : t;
+    y.v[1] = im ? t : y.v[1];
+  }
+  __host__ __device__ static __forceinline__ double inv_lead(const real& r) { return rcp_rn(r.h); }
+  __host__ __device__ static __forceinline__ void div_real_part(const Fp&, elem& q, const elem& a, const real& r,
+                                                               double, int part) {
+    const bool im = part != 0;
+    const double v = div_rn(im ? a.v[1] : a.v[0], r.h);
+    q.v[0] = im ? q.v[0] : v;
+    q.v[1] = im ? v : q.v[1];
+  }
+  __host__ __device__ static __forceinline__ void mul_real_part(const Fp& f, elem& q, const elem& a, const real& r,
+                                                               int part) {
+    const bool im = part != 0;
+    const double v = f.mul(im ? a.v[1] : a.v[0], r.h);
+    q.v[0] = im ? q.v[0] : v;
+    q.v[1] = im ? v : q.v[1];
+  }
+  __host__ __device__ static __forceinline__ elem from_real(const real& r) { return elem{{r.h, 0.0}}; }
+  __host__ __device__ static __forceinline__ real inv_real(const Fp&, const real& r) { return real{div_rn(1.0, r.h)}; }
+  __host__ __device__ static __forceinline__ real sqrt(const Fp&, const real& s) {
+    return real{s.h > 0.0 ? sqrt_rn(s.h) : 0.0};
+  }
+  __host__ __device__ static __forceinline__ bool positive(const real& r) { return r.h > 0.0 && finite64(r.h); }
+};
+
+// =====================================================================================
 // Double-double
 // =====================================================================================
 struct DD {

@@ -26,6 +26,7 @@ int launch_kernel(const Params& pr, int grid, size_t smem, cudaStream_t stream) 
   return (int)e;
 }
 
+int launch_d(const Params& pr, int grid, size_t smem, cudaStream_t stream);
 int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream);
 int launch_qd(const Params& pr, int grid, size_t smem, cudaStream_t stream);
 
