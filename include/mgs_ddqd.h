@@ -66,6 +66,27 @@ int mgs_last_cuda_error(void);
 size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs);
 
 /*
+ * How a single-system call of these sizes is laid out on the current device (no
+ * counterpart in the paper; for tests and tuning).
+ *   out[0] Br  row blocks (CTAs per column group), out[1] Bc  column groups,
+ *   out[2] h   rows per row block, out[3] kernel:
+ *     0  grid-barrier kernel: one grid-wide barrier per elimination step;
+ *     1  cluster schedule on hardware thread-block clusters (the Br CTAs of a column
+ *        group form one cluster and exchange Gram partials through distributed shared
+ *        memory; Br <= 8);
+ *     2  the same schedule on software groups (the Br CTAs meet at a counter in global
+ *        memory and exchange partials through L2; every SM usable).
+ *   The default is 1 for limbs 1 and 2 (0 where clusters cannot be formed) and 0 for
+ *   limbs 4: measured on GB300, the cluster schedule hides the per-step latency that
+ *   dominates the cheaper arithmetic, while quad double is bound by FP64 throughput.
+ *   The environment variable MGS_KERNEL = grid | cluster | group, read at each call,
+ *   forces a kernel (cluster falls back to grid where clusters cannot be formed);
+ *   MGS_ROWS = h overrides the rows per row block (default 64).
+ * Returns MGS_OK, MGS_EINVAL or MGS_ENOSPACE (no layout fits shared memory).
+ */
+int mgs_plan_query(int limbs, int m, int n, int with_rhs, int* out);
+
+/*
  * QR decomposition A = Q R by modified Gram-Schmidt (Section 3, Figure 1): for
  * k = 1..n, r_kk = sqrt(a_k^H a_k), q_k = a_k / r_kk, and for j > k
  * r_kj = q_k^H a_j, a_j = a_j - r_kj q_k, with x^H y = sum_l conj(x_l) y_l.

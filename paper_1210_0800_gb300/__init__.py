@@ -22,6 +22,7 @@ from ._binding import (  # noqa: F401
     mgs_qr_d,
     mgs_qr_dd,
     mgs_qr_qd,
+    mgs_plan_query,
     mgs_workspace_bytes,
 )
 from .autograd import LeastSquares, lstsq  # noqa: F401,E402

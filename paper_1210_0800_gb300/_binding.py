@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
            "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
-           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched"]
+           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched", "mgs_plan_query"]
 
 
 class MgsTune(ctypes.Structure):
@@ -55,6 +55,8 @@ def load(path: str | None = None):
     lib.mgs_last_cuda_error.restype = i
     lib.mgs_workspace_bytes.restype = sz
     lib.mgs_workspace_bytes.argtypes = [i, i, i, i]
+    lib.mgs_plan_query.restype = i
+    lib.mgs_plan_query.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int)]
     qr_args = [dp, i, dp, i, i, i, vp, sz, vp, vp]
     ls_args = [dp, i, dp, dp, dp, i, dp, i, i, vp, sz, vp, vp]
     for name in ("mgs_qr_d", "mgs_qr_dd", "mgs_qr_qd"):
@@ -215,6 +217,16 @@ def mgs_qr_qd(A, R=None, workspace=None, status=None, stream=None):
 
 def mgs_workspace_bytes(limbs: int, m: int, n: int, with_rhs: bool = True) -> int:
     return workspace_bytes(limbs, m, n, with_rhs)
+
+
+def mgs_plan_query(limbs: int, m: int, n: int, with_rhs: bool = True) -> dict:
+    """Layout of a single-system call on the current device: row blocks Br, column groups
+    Bc, rows per block h and the kernel ("grid", "cluster" or "group")."""
+    out = (ctypes.c_int * 4)()
+    rc = load().mgs_plan_query(limbs, m, n, 1 if with_rhs else 0, out)
+    if rc != 0:
+        raise MGSError(rc, "mgs_plan_query")
+    return dict(Br=out[0], Bc=out[1], h=out[2], kernel=("grid", "cluster", "group")[out[3]])
 
 
 # ----------------------------------------------------------------------------- batched

@@ -8,6 +8,22 @@
 #include "../../include/mgs_ddqd.h"
 #include "launch.cuh"
 
+namespace mgs {
+int launch_cluster_d(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
+int launch_cluster_dd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
+int launch_cluster_qd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
+int cluster_capacity_d(int cl, size_t smem);
+int cluster_capacity_dd(int cl, size_t smem);
+int cluster_capacity_qd(int cl, size_t smem);
+int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
+  return L == 1 ? launch_cluster_d(pr, grid, cl, smem, stream)
+                : L == 2 ? launch_cluster_dd(pr, grid, cl, smem, stream) : launch_cluster_qd(pr, grid, cl, smem, stream);
+}
+int cluster_capacity(int L, int cl, size_t smem) {
+  return L == 1 ? cluster_capacity_d(cl, smem) : L == 2 ? cluster_capacity_dd(cl, smem) : cluster_capacity_qd(cl, smem);
+}
+}  // namespace mgs
+
 namespace {
 
 thread_local int g_last_cuda = 0;
@@ -19,11 +35,21 @@ constexpr long long kTimeoutNs = 4000000000LL;  // 4 s: far above any legitimate
 struct Plan {
   int L, m, n, nc, aug;
   int Br, Bc, h, w;
+  int kind;  // 0 grid barrier per step, 1 hardware clusters, 2 software groups
   size_t smem;
-  size_t off_sync, off_flags, off_P, off_V, off_Y, off_R, off_G, off_T, total, zero_bytes;
+  size_t off_sync, off_gsync, off_flags, off_P, off_V, off_Y, off_R, off_G, off_T, total, zero_bytes;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Dynamic shared memory that keeps a second CTA off the SM: each CTA of the solve then has
+// the SM's FP64 unit to itself.
+size_t one_cta_per_sm_smem() {
+  int dev = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
+  return (size_t)per_sm / 2;
+}
 
 int device_sms() {
   int dev = 0, sms = 0;
@@ -43,23 +69,51 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   pl.aug = aug ? 1 : 0;
   pl.nc = n + pl.aug;
   const int E = 2 * L;
-  int h = 64;
+  // MGS_KERNEL = grid | cluster | group overrides the default choice: the cluster
+  // schedule on hardware clusters for complex double and double-double (where the
+  // per-step latency is a large share of a step), the grid-barrier kernel where hardware
+  // clusters cannot be formed and for quad double (where the FP64 throughput decides)
+  const char* kenv = std::getenv("MGS_KERNEL");
+  const int want = !kenv ? -1 : kenv[0] == 'g' && kenv[1] == 'r' && kenv[2] == 'i' ? 0 : kenv[0] == 'c' ? 1 : 2;
+  const char* henv = std::getenv("MGS_ROWS");  // rows per row block (tuning override)
+  int h = henv ? std::atoi(henv) : 64;
+  if (h < 8 || h > 1024) h = 64;
+  const size_t pad = one_cta_per_sm_smem();
+  auto padded = [&](size_t v) { return (pad > v && pad <= kMaxSmem) ? pad : v; };
   for (;;) {
-    int Br = (m + h - 1) / h;
+    const int Br = (m + h - 1) / h;
     if (Br > kMaxBr || Br > sms) return false;
-    int Bc = sms / Br;
-    if (Bc > pl.nc) Bc = pl.nc;
-    if (Bc < 1) return false;
+    const int Bc_grid = sms / Br < pl.nc ? sms / Br : pl.nc;
+    if (Bc_grid < 1) return false;
+    int kind = want < 0 ? (L <= 2 ? 1 : 0) : want, Bc = Bc_grid;
+    if (kind == 1) {
+      // hardware clusters: as many column groups as clusters fit at once
+      int cap = 0;
+      if (Br <= 8) {
+        for (int it = 0, Bt = Bc_grid; it < 3; ++it) {
+          const int wt = (pl.nc + Bt - 1) / Bt;
+          cap = mgs::cluster_capacity(L, Br, padded(mgs::cluster_smem_bytes(L, h, wt)));
+          if (cap <= 0 || Bt <= cap) break;
+          Bt = cap;
+        }
+      }
+      if (cap > 0) {
+        Bc = cap < Bc_grid ? cap : Bc_grid;
+      } else {
+        kind = 0;
+      }
+    }
     const int w = (pl.nc + Bc - 1) / Bc;
-    size_t smem = mgs::smem_bytes(L, h, w);
-    const size_t bs = sizeof(double) * ((size_t)(mgs::kBS + 1) * E) + 64;  // back substitution
+    size_t smem = kind == 0 ? mgs::smem_bytes(L, h, w) : mgs::cluster_smem_bytes(L, h, w);
+    const size_t bs = mgs::backsub_smem_bytes(L);
     if (bs > smem) smem = bs;
     if (smem <= kMaxSmem) {
       pl.Br = Br;
       pl.Bc = Bc;
       pl.h = h;
       pl.w = w;
-      pl.smem = smem;
+      pl.smem = padded(smem);
+      pl.kind = kind;
       break;
     }
     if (h <= 8) return false;
@@ -68,14 +122,19 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   size_t off = 0;
   pl.off_sync = off;
   off = align256(off + 64);
+  pl.off_gsync = off;  // per-group arrival counters, 128 bytes apart
+  off = align256(off + sizeof(unsigned) * 32 * (size_t)pl.Bc);
   pl.off_flags = off;
-  off = align256(off + sizeof(int) * (size_t)(pl.nc + 1) * pl.Br);
+  off = align256(off + sizeof(int) * (size_t)(pl.nc + 1) * pl.Br);  // pivot-ready flags
   pl.zero_bytes = off;
   const int ACC = (L == 1) ? mgs::D::ACC : (L == 2) ? mgs::DD::ACC : mgs::QD::ACC;
   pl.off_P = off;
-  off = align256(off + sizeof(double) * 2 * (size_t)pl.Br * pl.nc * ACC);
-  pl.off_V = off;
-  off = align256(off + sizeof(double) * 2 * (size_t)pl.Br * pl.h * E);
+  const size_t pdoubles = pl.kind == 0 ? 2 * (size_t)pl.Br * pl.nc * ACC
+                          : pl.kind == 2 ? mgs::group_partials_doubles(L, pl.Br, pl.Bc, (pl.nc + pl.Bc - 1) / pl.Bc)
+                                         : 0;
+  off = align256(off + sizeof(double) * pdoubles);
+  pl.off_V = off;  // published pivot rows: one slot per pivot (cluster schedule), two otherwise
+  off = align256(off + sizeof(double) * (size_t)(pl.kind != 0 ? pl.nc + 1 : 2) * pl.Br * pl.h * E);
   pl.off_Y = off;
   off = align256(off + sizeof(double) * (size_t)pl.nc * E);
   pl.off_R = off;
@@ -130,6 +189,7 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.Bc = pl.Bc;
   pr.h = pl.h;
   pr.sync = reinterpret_cast<unsigned*>(wb + pl.off_sync);
+  pr.gsync = reinterpret_cast<unsigned*>(wb + pl.off_gsync);
   pr.flags = reinterpret_cast<int*>(wb + pl.off_flags);
   pr.P = reinterpret_cast<double*>(wb + pl.off_P);
   pr.V = reinterpret_cast<double*>(wb + pl.off_V);
@@ -147,9 +207,13 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.trace = nullptr;
 #endif
   const int grid = pl.Br * pl.Bc;
-  const int rc = (L == 1)   ? mgs::launch_d(pr, grid, pl.smem, st)
-                 : (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st)
-                            : mgs::launch_qd(pr, grid, pl.smem, st);
+  int rc;
+  if (pl.kind == 1)
+    rc = mgs::launch_cluster(L, pr, grid, pl.Br, pl.smem, st);
+  else
+    rc = (L == 1) ? mgs::launch_d(pr, grid, pl.smem, st, pl.kind)
+         : (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st, pl.kind)
+                    : mgs::launch_qd(pr, grid, pl.smem, st, pl.kind);
   if (rc != 0) {
     g_last_cuda = rc;
     return MGS_ECUDA;
@@ -201,6 +265,17 @@ size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs) {
   Plan pl;
   if (!make_plan(limbs, m, n, with_rhs, pl)) return 0;
   return pl.total;
+}
+
+int mgs_plan_query(int limbs, int m, int n, int with_rhs, int* out) {
+  if (!out || (limbs != 1 && limbs != 2 && limbs != 4) || m < 1 || n < 1 || m < n) return MGS_EINVAL;
+  Plan pl;
+  if (!make_plan(limbs, m, n, with_rhs, pl)) return MGS_ENOSPACE;
+  out[0] = pl.Br;
+  out[1] = pl.Bc;
+  out[2] = pl.h;
+  out[3] = pl.kind;
+  return MGS_OK;
 }
 
 int mgs_qr_d(double* A, int lda, double* R, int ldr, int m, int n, void* workspace, size_t workspace_bytes,

@@ -2,7 +2,11 @@
 #include "launch.cuh"
 
 namespace mgs {
-int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream) {
-  return launch_kernel<DD>(pr, grid, smem, stream);
+int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
+  return launch_kernel<DD>(pr, grid, smem, stream, kind);
 }
+int launch_cluster_dd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
+  return launch_cluster_kernel<DD>(pr, grid, cl, smem, stream);
+}
+int cluster_capacity_dd(int cl, size_t smem) { return max_active_clusters<DD>(cl, smem); }
 }  // namespace mgs

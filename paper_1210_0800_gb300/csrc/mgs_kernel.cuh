@@ -57,8 +57,9 @@ struct Params {
   int m, n, nc, aug;
   int Br, Bc, h;
   unsigned* sync;  // [0] barrier arrivals, [1] abort flag
+  unsigned* gsync;  // per-column-group arrival counters, 32 apart (group kernel)
   int* flags;      // nc * Br pivot-ready flags
-  double* P;       // partial Gram rows: 2 * Br * nc * ACC
+  double* P;       // partial Gram rows: 2 * Br * nc * ACC (group kernel: its partial buffers)
   double* V;       // published pivot rows: 2 * Br * h * 2L
   double* Y;       // y = Q^H b (and the back-substitution right-hand side): nc * 2L
   double* Gd;      // pivot norms G_kk = ||a_k||^2: nc * L
@@ -77,9 +78,21 @@ struct Params {
     if (threadIdx.x == 0 && pr.trace)                                                      \
       pr.trace[((size_t)(step) * gridDim.x + blockIdx.x) * 8 + (ph)] = globaltimer();       \
   } while (0)
+// the SM a CTA runs on (slot 7 of the step-0 record)
+#define MGS_TR_SMID()                                                                       \
+  do {                                                                                     \
+    if (threadIdx.x == 0 && pr.trace) {                                                    \
+      unsigned sid;                                                                        \
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sid));                                     \
+      pr.trace[(size_t)blockIdx.x * 8 + 7] = sid;                                          \
+    }                                                                                      \
+  } while (0)
 #else
 #define MGS_TR(step, ph) \
   do {                   \
+  } while (0)
+#define MGS_TR_SMID() \
+  do {                \
   } while (0)
 #endif
 
@@ -244,6 +257,221 @@ __host__ __device__ inline size_t smem_bytes(int L, int h, int w) {
 
 // Back substitution block size (rows of R solved by one CTA between grid barriers).
 constexpr int kBS = 32;
+// Shared memory of the back substitution's diagonal block: right-hand side and t_jk.
+__host__ __device__ inline size_t backsub_smem_bytes(int L) {
+  return sizeof(double) * (size_t)(kBS + kBS * kBS) * 2 * L + 64;
+}
+
+// Normalisation (Q = a_k / r_kk from the CTA's resident tile, R = c r_kk), then the
+// back substitution; shared by the single-system kernels.  The tile layout is the one
+// both kernels keep in shared memory: slot s of column c + s Bc, limb planes of h rows.
+template <class Ar>
+__device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, double* sm, int p, int c) {
+  constexpr int L = Ar::L, E = 2 * L;
+  using elem = typename Ar::elem;
+  using real = typename Ar::real;
+  using pacc = typename Ar::pacc;
+  constexpr int PACC = Ar::PACC;
+  const Fp f{pr.one, pr.nzero};
+  const int tid = threadIdx.x;
+  const int Bc = pr.Bc, Br = pr.Br, nc = pr.nc, h = pr.h;
+  const int r0 = p * h;
+  const int hr = max(0, min(h, pr.m - r0));
+  const int w = (nc - c + Bc - 1) / Bc;
+  double* tile = sm;
+  auto col_of = [&](int s) { return c + s * Bc; };
+  auto ld_real = [&](const double* src) {
+    real r;
+    double* d = reinterpret_cast<double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) d[q] = __ldcg(src + q);
+    return r;
+  };
+  auto st_real = [&](double* dst, const real& r) {
+    const double* d = reinterpret_cast<const double*>(&r);
+#pragma unroll
+    for (int q = 0; q < L; ++q) dst[q] = d[q];
+  };
+  // ---------------------------------------------------------------- normalisation
+  const int nthreads = gridDim.x * kThreads;
+  const int gtid = blockIdx.x * kThreads + tid;
+  // (E1) r_kk = sqrt(G_kk) and 1 / r_kk for every column, spread over all threads
+  for (int k = gtid; k < nc; k += nthreads) {
+    const real G = ld_real(pr.Gd + (size_t)k * L);
+    const real r = Ar::sqrt(f, G);
+    st_real(pr.Rd + (size_t)k * L, r);
+    if (Ar::positive(r)) st_real(pr.Ri + (size_t)k * L, Ar::inv_real(f, r));
+    if (pr.aug && k == nc - 1 && pr.z) st_real(pr.z, r);
+  }
+  grid_barrier(pr, epoch);
+  MGS_TR(nc, 1);
+  // (E2) q_j = a_j / r_jj for the own columns (the tile holds the unnormalised columns)
+  {
+    const int nq = pr.n;  // columns that are normalised
+    const int wq = (nq - c + Bc - 1) / Bc;
+    if (wq > 0 && hr > 0) {
+      const int tot = wq * hr * 2;
+      for (int idx = tid; idx < tot; idx += kThreads) {
+        const int part = idx & 1, rest = idx >> 1;
+        const int s = rest / hr, l = rest % hr, j = col_of(s);
+        const real r = ld_real(pr.Rd + (size_t)j * L);
+        if (!Ar::positive(r)) continue;
+        const elem a = sm_load<Ar>(tile + (size_t)s * E * h, h, l);
+        elem q = a;
+        Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
+#pragma unroll
+        for (int qq = 0; qq < L; ++qq) pr.A[((size_t)j * pr.lda + r0 + l) * E + part * L + qq] = q.v[part * L + qq];
+      }
+    }
+  }
+  // (E3) r_kj = c_kj r_kk for the own columns (rows k < j split over the row blocks),
+  //      y_k = c_kn r_kk, and the real diagonal r_jj
+  {
+    for (int s = 0; s < w; ++s) {
+      const int j = col_of(s);
+      const int tot = j * 2;  // (k, part) pairs with k < j
+      for (int idx = p * kThreads + tid; idx < tot; idx += Br * kThreads) {
+        const int k = idx >> 1, part = idx & 1;
+        double* dst = (j < pr.n) ? pr.R + ((size_t)j * pr.ldr + k) * E : pr.Y + (size_t)k * E;
+        elem cc;
+#pragma unroll
+        for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < L; ++q) cc.v[part * L + q] = __ldcg(dst + part * L + q);
+        elem r = cc;
+        Ar::mul_real_part(f, r, cc, ld_real(pr.Rd + (size_t)k * L), part);
+#pragma unroll
+        for (int q = 0; q < L; ++q) dst[part * L + q] = r.v[part * L + q];
+      }
+      if (p == 0 && tid == 0 && j < pr.n) g_store<Ar>(pr.R + ((size_t)j * pr.ldr + j) * E,
+                                                     Ar::from_real(ld_real(pr.Rd + (size_t)j * L)));
+    }
+  }
+
+  // ---------------------------------------------------------------- back substitution
+  if (!pr.aug || pr.x == nullptr) return;
+  grid_barrier(pr, epoch);
+  // Figure 3 on the column-scaled system: with D = diag(r_kk), R x = y is solved as
+  // (R D^-1)(D x) = y.  The scaled columns t_jk = r_jk / r_kk are formed once, in parallel;
+  // the sequential chain is then x~_k = y_k and y_j -= t_jk x~_k (one update per link
+  // instead of a product and an update), and x_k = x~_k / r_kk (a true division) for all k
+  // in parallel at the end.
+  const int n = pr.n;
+  {
+    const long long tot = (long long)n * (n - 1);  // (j < k) pairs x 2 parts
+    for (long long idx = gtid; idx < tot; idx += nthreads) {
+      const int part = (int)(idx & 1);
+      const long long pi = idx >> 1;
+      int k = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pi)) * 0.5);  // pi = k(k-1)/2 + j
+      while ((long long)k * (k - 1) / 2 > pi) --k;
+      while ((long long)(k + 1) * k / 2 <= pi) ++k;
+      const int j = (int)(pi - (long long)k * (k - 1) / 2);
+      elem r;
+#pragma unroll
+      for (int q = 0; q < E; ++q) r.v[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < L; ++q) r.v[part * L + q] = __ldcg(pr.R + ((size_t)k * pr.ldr + j) * E + part * L + q);
+      elem t = r;
+      Ar::mul_real_part(f, t, r, ld_real(pr.Ri + (size_t)k * L), part);
+#pragma unroll
+      for (int q = 0; q < L; ++q) pr.Rt[((size_t)k * n + j) * E + part * L + q] = t.v[part * L + q];
+    }
+  }
+  grid_barrier(pr, epoch);
+  MGS_TR(nc, 2);
+  // blocks of kBS rows: CTA 0 runs the chain of the diagonal block (its t_jk staged in
+  // shared memory), then every CTA applies the block's x~ to the rows above it.
+  for (int e = n; e > 0; e -= kBS) {
+    const int s = max(0, e - kBS);
+    const int nbk = e - s;
+    if (blockIdx.x == 0) {
+      double* ys = sm;                          // nbk * E, row k at (k - s) * E
+      double* tb = sm + (size_t)kBS * E;        // t_jk (j < k in the block) at ((k - s) kBS + j - s) E
+      for (int i = tid; i < nbk; i += kThreads) {
+        const elem v = g_load_cg<Ar>(pr.Y + (size_t)(s + i) * E);
+#pragma unroll
+        for (int q = 0; q < E; ++q) ys[(size_t)i * E + q] = v.v[q];
+      }
+      for (int i = tid; i < nbk * nbk; i += kThreads) {
+        const int kk = i / nbk, jj = i % nbk;
+        if (jj >= kk) continue;
+        const elem v = g_load_cg<Ar>(pr.Rt + ((size_t)(s + kk) * n + s + jj) * E);
+#pragma unroll
+        for (int q = 0; q < E; ++q) tb[((size_t)kk * kBS + jj) * E + q] = v.v[q];
+      }
+      __syncthreads();
+      for (int k = e - 1; k >= s; --k) {
+        elem xk;
+#pragma unroll
+        for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
+        if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
+        for (int t = tid; t < 2 * (k - s); t += kThreads) {
+          const int j = s + (t >> 1), part = t & 1;
+          double* yj = ys + (size_t)(j - s) * E;
+          elem y = sm_load_part<Ar>(yj, 1, 0, part);
+          Ar::update_part(f, y, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (j - s)) * E, 1, 0), xk, part);
+#pragma unroll
+          for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
+        }
+        __syncthreads();
+      }
+    }
+    if (s == 0) break;
+    grid_barrier(pr, epoch);
+    // rows j < s: y_j -= sum_{k in [s, e)} t_jk x~_k; 8 lanes per (row, part) each sum a
+    // share of the terms, a shuffle tree combines them, lane 0 of the group subtracts
+    {
+      constexpr int G = 8;
+      const int tot = s * 2 * G;
+      const int span = ((tot + nthreads - 1) / nthreads) * nthreads;  // uniform trip count
+      for (int idx = gtid; idx < span; idx += nthreads) {
+        const bool act = idx < tot;
+        const int grp = idx / G, ch = idx % G;
+        const int j = grp >> 1, part = grp & 1;
+        pacc a;
+        Ar::pzero(a);
+        if (act)
+          for (int k = e - 1 - ch; k >= s; k -= G)
+            Ar::mul_acc_part(f, a, g_load_cg<Ar>(pr.Rt + ((size_t)k * n + j) * E),
+                             g_load_cg<Ar>(pr.x + (size_t)k * E), part);
+        for (int off = 1; off < G; off <<= 1) {
+          pacc o;
+          const double* sa = reinterpret_cast<const double*>(&a);
+          double* so = reinterpret_cast<double*>(&o);
+#pragma unroll
+          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], off);
+          Ar::pcombine(f, a, o);
+        }
+        if (act && ch == 0) {
+          double y[L];
+          double* yp = pr.Y + (size_t)j * E + part * L;
+#pragma unroll
+          for (int q = 0; q < L; ++q) y[q] = __ldcg(yp + q);
+          Ar::psub(f, y, a);
+#pragma unroll
+          for (int q = 0; q < L; ++q) yp[q] = y[q];
+        }
+      }
+    }
+    grid_barrier(pr, epoch);
+  }
+  grid_barrier(pr, epoch);
+  // x_k = x~_k / r_kk
+  for (int idx = gtid; idx < 2 * n; idx += nthreads) {
+    const int k = idx >> 1, part = idx & 1;
+    elem xt;
+#pragma unroll
+    for (int q = 0; q < E; ++q) xt.v[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < L; ++q) xt.v[part * L + q] = __ldcg(pr.x + (size_t)k * E + part * L + q);
+    const real r = ld_real(pr.Rd + (size_t)k * L);
+    elem xv = xt;
+    Ar::div_real_part(f, xv, xt, r, Ar::inv_lead(r), part);
+#pragma unroll
+    for (int q = 0; q < L; ++q) pr.x[(size_t)k * E + part * L + q] = xv.v[part * L + q];
+  }
+  MGS_TR(nc, 3);
+}
 
 // ------------------------------------------------------------------ the kernel
 template <class Ar>
@@ -290,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     for (int q = 0; q < L; ++q) dst[q] = d[q];
   };
 
+  MGS_TR_SMID();
   // ---------------------------------------------------------------- load the tile
   if (tid == 0) iflag[0] = 0;
   __syncthreads();
@@ -560,176 +789,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   grid_barrier(pr, epoch);
   MGS_TR(nc, 0);
 
-  // ---------------------------------------------------------------- normalisation
-  const int nthreads = gridDim.x * kThreads;
-  const int gtid = blockIdx.x * kThreads + tid;
-  // (E1) r_kk = sqrt(G_kk) and 1 / r_kk for every column, spread over all threads
-  for (int k = gtid; k < nc; k += nthreads) {
-    const real G = ld_real(pr.Gd + (size_t)k * L);
-    const real r = Ar::sqrt(f, G);
-    st_real(pr.Rd + (size_t)k * L, r);
-    if (Ar::positive(r)) st_real(pr.Ri + (size_t)k * L, Ar::inv_real(f, r));
-    if (pr.aug && k == nc - 1 && pr.z) st_real(pr.z, r);
-  }
-  grid_barrier(pr, epoch);
-  MGS_TR(nc, 1);
-  // (E2) q_j = a_j / r_jj for the own columns (the tile holds the unnormalised columns)
-  {
-    const int nq = pr.n;  // columns that are normalised
-    const int wq = (nq - c + Bc - 1) / Bc;
-    if (wq > 0 && hr > 0) {
-      const int tot = wq * hr * 2;
-      for (int idx = tid; idx < tot; idx += kThreads) {
-        const int part = idx & 1, rest = idx >> 1;
-        const int s = rest / hr, l = rest % hr, j = col_of(s);
-        const real r = ld_real(pr.Rd + (size_t)j * L);
-        if (!Ar::positive(r)) continue;
-        const elem a = sm_load<Ar>(tile + (size_t)s * E * h, h, l);
-        elem q = a;
-        Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
-#pragma unroll
-        for (int qq = 0; qq < L; ++qq) pr.A[((size_t)j * pr.lda + r0 + l) * E + part * L + qq] = q.v[part * L + qq];
-      }
-    }
-  }
-  // (E3) r_kj = c_kj r_kk for the own columns (rows k < j split over the row blocks),
-  //      y_k = c_kn r_kk, and the real diagonal r_jj
-  {
-    for (int s = 0; s < w; ++s) {
-      const int j = col_of(s);
-      const int tot = j * 2;  // (k, part) pairs with k < j
-      for (int idx = p * kThreads + tid; idx < tot; idx += Br * kThreads) {
-        const int k = idx >> 1, part = idx & 1;
-        double* dst = (j < pr.n) ? pr.R + ((size_t)j * pr.ldr + k) * E : pr.Y + (size_t)k * E;
-        elem cc;
-#pragma unroll
-        for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
-#pragma unroll
-        for (int q = 0; q < L; ++q) cc.v[part * L + q] = __ldcg(dst + part * L + q);
-        elem r = cc;
-        Ar::mul_real_part(f, r, cc, ld_real(pr.Rd + (size_t)k * L), part);
-#pragma unroll
-        for (int q = 0; q < L; ++q) dst[part * L + q] = r.v[part * L + q];
-      }
-      if (p == 0 && tid == 0 && j < pr.n) g_store<Ar>(pr.R + ((size_t)j * pr.ldr + j) * E,
-                                                     Ar::from_real(ld_real(pr.Rd + (size_t)j * L)));
-    }
-  }
-
-  // ---------------------------------------------------------------- back substitution
-  if (!pr.aug || pr.x == nullptr) return;
-  grid_barrier(pr, epoch);
-  // Figure 3 on the column-scaled system: with D = diag(r_kk), R x = y is solved as
-  // (R D^-1)(D x) = y.  The scaled columns t_jk = r_jk / r_kk are formed once, in parallel;
-  // the sequential chain is then x~_k = y_k and y_j -= t_jk x~_k (one update per link
-  // instead of a product and an update), and x_k = x~_k / r_kk (a true division) for all k
-  // in parallel at the end.
-  const int n = pr.n;
-  {
-    const long long tot = (long long)n * (n - 1);  // (j < k) pairs x 2 parts
-    for (long long idx = gtid; idx < tot; idx += nthreads) {
-      const int part = (int)(idx & 1);
-      const long long pi = idx >> 1;
-      int k = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pi)) * 0.5);  // pi = k(k-1)/2 + j
-      while ((long long)k * (k - 1) / 2 > pi) --k;
-      while ((long long)(k + 1) * k / 2 <= pi) ++k;
-      const int j = (int)(pi - (long long)k * (k - 1) / 2);
-      elem r;
-#pragma unroll
-      for (int q = 0; q < E; ++q) r.v[q] = 0.0;
-#pragma unroll
-      for (int q = 0; q < L; ++q) r.v[part * L + q] = __ldcg(pr.R + ((size_t)k * pr.ldr + j) * E + part * L + q);
-      elem t = r;
-      Ar::mul_real_part(f, t, r, ld_real(pr.Ri + (size_t)k * L), part);
-#pragma unroll
-      for (int q = 0; q < L; ++q) pr.Rt[((size_t)k * n + j) * E + part * L + q] = t.v[part * L + q];
-    }
-  }
-  grid_barrier(pr, epoch);
-  MGS_TR(nc, 2);
-  // blocks of kBS rows: CTA 0 runs the chain of the diagonal block, then every CTA
-  // applies the block's x~ to the rows above it.
-  for (int e = n; e > 0; e -= kBS) {
-    const int s = max(0, e - kBS);
-    if (blockIdx.x == 0) {
-      double* ys = sm;  // (e - s) * E, row k at (k - s) * E
-      for (int i = tid; i < e - s; i += kThreads) {
-        const elem v = g_load_cg<Ar>(pr.Y + (size_t)(s + i) * E);
-#pragma unroll
-        for (int q = 0; q < E; ++q) ys[(size_t)i * E + q] = v.v[q];
-      }
-      __syncthreads();
-      for (int k = e - 1; k >= s; --k) {
-        elem xk;
-#pragma unroll
-        for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
-        if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
-        for (int t = tid; t < 2 * (k - s); t += kThreads) {
-          const int j = s + (t >> 1), part = t & 1;
-          double* yj = ys + (size_t)(j - s) * E;
-          elem y = sm_load_part<Ar>(yj, 1, 0, part);
-          Ar::update_part(f, y, g_load_cg<Ar>(pr.Rt + ((size_t)k * n + j) * E), xk, part);
-#pragma unroll
-          for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
-        }
-        __syncthreads();
-      }
-    }
-    if (s == 0) break;
-    grid_barrier(pr, epoch);
-    // rows j < s: y_j -= sum_{k in [s, e)} t_jk x~_k; 8 lanes per (row, part) each sum a
-    // share of the terms, a shuffle tree combines them, lane 0 of the group subtracts
-    {
-      constexpr int G = 8;
-      const int tot = s * 2 * G;
-      const int span = ((tot + nthreads - 1) / nthreads) * nthreads;  // uniform trip count
-      for (int idx = gtid; idx < span; idx += nthreads) {
-        const bool act = idx < tot;
-        const int grp = idx / G, ch = idx % G;
-        const int j = grp >> 1, part = grp & 1;
-        pacc a;
-        Ar::pzero(a);
-        if (act)
-          for (int k = e - 1 - ch; k >= s; k -= G)
-            Ar::mul_acc_part(f, a, g_load_cg<Ar>(pr.Rt + ((size_t)k * n + j) * E),
-                             g_load_cg<Ar>(pr.x + (size_t)k * E), part);
-        for (int off = 1; off < G; off <<= 1) {
-          pacc o;
-          const double* sa = reinterpret_cast<const double*>(&a);
-          double* so = reinterpret_cast<double*>(&o);
-#pragma unroll
-          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], off);
-          Ar::pcombine(f, a, o);
-        }
-        if (act && ch == 0) {
-          double y[L];
-          double* yp = pr.Y + (size_t)j * E + part * L;
-#pragma unroll
-          for (int q = 0; q < L; ++q) y[q] = __ldcg(yp + q);
-          Ar::psub(f, y, a);
-#pragma unroll
-          for (int q = 0; q < L; ++q) yp[q] = y[q];
-        }
-      }
-    }
-    grid_barrier(pr, epoch);
-  }
-  grid_barrier(pr, epoch);
-  // x_k = x~_k / r_kk
-  for (int idx = gtid; idx < 2 * n; idx += nthreads) {
-    const int k = idx >> 1, part = idx & 1;
-    elem xt;
-#pragma unroll
-    for (int q = 0; q < E; ++q) xt.v[q] = 0.0;
-#pragma unroll
-    for (int q = 0; q < L; ++q) xt.v[part * L + q] = __ldcg(pr.x + (size_t)k * E + part * L + q);
-    const real r = ld_real(pr.Rd + (size_t)k * L);
-    elem xv = xt;
-    Ar::div_real_part(f, xv, xt, r, Ar::inv_lead(r), part);
-#pragma unroll
-    for (int q = 0; q < L; ++q) pr.x[(size_t)k * E + part * L + q] = xv.v[part * L + q];
-  }
-  MGS_TR(nc, 3);
+  mgs_epilogue<Ar>(pr, epoch, sm, p, c);
 }
 
 }  // namespace mgs
