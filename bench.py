@@ -50,6 +50,14 @@ WORKLOADS = {
     "d_256": (1, 256, 256, False),
 }
 DEFAULT = "c1_qd_320x256"
+SWEEP = ["dd_64", "dd_128", "dd_256", "dd_512", "qd_64", "qd_128", "qd_256", "qd_512"]
+
+
+def hbm_bytes(L: int, m: int, n: int) -> int:
+    """Algorithmic HBM bytes of one solve: [A b] read, Q and the residual column written,
+    x and the upper triangle of R written."""
+    e = 16 * L
+    return e * (2 * m * (n + 1) + n + n * (n + 1) // 2)
 # batched workloads: name -> (limbs, batch, n range, extra rows range)
 BATCHED = {
     "c3_dd_batched_512": (2, 512, (16, 192), (0, 16)),
@@ -67,6 +75,20 @@ COST = {
 # FP64 peak: 152 SMs x 4 sub-partitions x 0.5 FP64 lanes/clk (one DFMA warp-instruction
 # per 64 cycles per sub-partition, measured) at the 2070 MHz maximum SM clock.
 SMS, FP64_LANES_PER_CLK_SM = 152, 2.0
+
+
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+L2_NOTE = ("every step reads its own distinct inputs, untouched since a %d MB write flushed L2 after "
+           "setup and warm-up (only the workspace is reused across steps)" % (L2_FLUSH_BYTES >> 20))
+
+
+def flush_l2(dev):
+    import torch
+
+    buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    buf.fill_(1)
+    torch.cuda.synchronize(dev)
+    del buf
 
 
 def fp64_ops(L: int, m: int, n: int) -> float:
@@ -232,7 +254,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     K, W = args.steps, args.warmup
     total = K + W
     # distinct systems for every step (rank-dependent seeds: replicas solve different systems)
-    seeds = [inputs.system_seed(inputs.BASE_SEED + 1, rank * 100000 + i) for i in range(total)]
+    seeds = [inputs.system_seed(inputs.workload_seed(args.workload), rank * 100000 + i) for i in range(total)]
     host = [inputs.system(m, n, L, s, extreme=extreme) for s in seeds]
     As = [torch.from_numpy(h[0]).to(dev) for h in host]
     bs = [torch.from_numpy(h[2]).to(dev) for h in host]
@@ -253,6 +275,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush_l2(dev)
     clocks = ClockSampler(local)
     time.sleep(0.3)
     barrier()
@@ -322,7 +345,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "extreme": extreme,
-                   "systems_per_step": 1, "l2": "inputs larger than L2 (every step a distinct 5 MB+ system)",
+                   "systems_per_step": 1, "l2": L2_NOTE,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": world / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -334,6 +357,8 @@ def run_gpu(args, L, m, n, extreme, rank, world):
                              "(%.4g) / CUDA-event time per solve; each instruction counted as one FMA slot "
                              "(2 flops) like the peak (152 SMs x 2 DFMA/clk x %.0f MHz)" % (ops, sm_max)},
         "kernel_ms": kernel_ms,
+        "hbm": {"bytes_per_solve": hbm_bytes(L, m, n), "achieved_gbs": hbm_bytes(L, m, n) / kernel_ms / 1e6,
+                "note": "algorithmic bytes / kernel time; the solve is FP64-bound, not HBM-bound"},
         "status_errors": len(bad),
     }
     if clk:
@@ -343,15 +368,6 @@ def run_gpu(args, L, m, n, extreme, rank, world):
         line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": desc}
     print(json.dumps(line))
     return 0
-
-
-def make_batch_host(L, batch, n_rng, e_rng, seed):
-    ms, ns = inputs.ragged_shapes(batch, seed, n_rng[0], n_rng[1], e_rng[0], e_rng[1])
-    systems = []
-    for i, (m, n) in enumerate(zip(ms, ns)):
-        A, _, b = inputs.system(int(m), int(n), L, inputs.system_seed(seed, i))
-        systems.append((A, b))
-    return systems
 
 
 def run_gpu_batched(args, rank, world):
@@ -368,7 +384,7 @@ def run_gpu_batched(args, rank, world):
     dev = torch.device("cuda", local)
     K, W = args.steps, args.warmup
     seed0 = inputs.BASE_SEED + 3
-    host = make_batch_host(L, batch, n_rng, e_rng, inputs.system_seed(seed0, rank))
+    host = inputs.ragged_batch(L, batch, n_rng, e_rng, inputs.system_seed(seed0, rank))
     ops = sum(fp64_ops(L, A.shape[1], A.shape[0]) for A, _ in host)
     # distinct device copies of the batch for warm-up + timed steps (pools are overwritten)
     base = mg.make_batch(host, dev)
@@ -396,6 +412,7 @@ def run_gpu_batched(args, rank, world):
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush_l2(dev)
     clocks = ClockSampler(local)
     time.sleep(0.3)
     if world > 1:
@@ -460,7 +477,7 @@ def run_gpu_batched(args, rank, world):
                    "m_minus_n_range": list(e_rng), "max_m": base.max_m, "max_n": base.max_n,
                    "launch": "one persistent launch per step, replayed from a CUDA graph",
                    "tune": {"threads": best[0], "ctas_per_sm": best[1], "candidates_ms": times},
-                   "l2": "inputs larger than L2 (every step a distinct %.0f MB batch)" % (h2d / 2 ** 20),
+                   "l2": L2_NOTE,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": world * batch / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": base.x_pool.numel() * 8},
@@ -525,6 +542,7 @@ def run_gpu_diff(args, rank, world):
     for i in range(W):
         step(i)
     torch.cuda.synchronize(dev)
+    flush_l2(dev)
     clocks = ClockSampler(local)
     time.sleep(0.3)
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,7 +574,7 @@ def run_gpu_diff(args, rank, world):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "systems_per_step": B,
                    "step": "forward solve + adjoint (dL/dA, dL/db for L = sum |x|^2) via torch.autograd.Function",
-                   "l2": "distinct input copies per step (%.0f MB)" % (A0.numel() * 8 / 2 ** 20),
+                   "l2": L2_NOTE,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": None,
         "gpu_launches": 2 * K,
@@ -582,6 +600,8 @@ def main(argv=None):
     ap.add_argument("--seq-sample", type=int, default=64, help="systems solved one by one for the comparison")
     ap.add_argument("--ref-seconds", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="one line per point of the m = n in {64, 128, 256, 512} DD and QD sweep")
     args = ap.parse_args(argv)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -599,6 +619,15 @@ def main(argv=None):
             L, batch, n_rng, e_rng = BATCHED[args.workload]
             return run_reference(args, L, (n_rng[0] + n_rng[1]) // 2 + 8, (n_rng[0] + n_rng[1]) // 2, rank, world)
         return run_gpu_batched(args, rank, world)
+    if args.sweep and args.impl == "ours":
+        args.no_cpu_baseline = True
+        for wl in SWEEP:
+            args.workload = wl
+            L, m, n, extreme = WORKLOADS[wl]
+            rc = run_gpu(args, L, m, n, extreme, rank, world)
+            if rc:
+                return rc
+        return 0
     L, m, n, extreme = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, L, m, n, rank, world)

@@ -216,6 +216,55 @@ int ls_adjoint_qd_batched(const double* Q_pool, const double* R_pool, const doub
 int ls_solve_dd_noalloc(double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n,
                         int32_t* dev_status, void* stream);
 
+/*
+ * Newton corrector on the device (Section 7: Newton's method is the corrector of path
+ * tracking; the Jacobian and the system stay on the GPU, only solutions go back).  The
+ * caller evaluates F(x) and its Jacobian J = F'(x) on the device; this library does not
+ * evaluate functions.  One step:
+ *   f_norm[i] = ||F||_inf; solve min ||F - J s|| by MGS on [J F] and back substitution
+ *   (as ls_solve_*); x <- x - s; dx_norm[i] = ||s||_inf, x_norm[i] = ||x||_inf,
+ *   z[i] = ||F - J s||; done = 1 when dx_norm[i] <= tol * x_norm[i].
+ * Norms are taken on the leading limbs (|v| = hypot(re_0, im_0)).
+ * While done != 0 at the start of a step, the step does nothing (the gate is read on the
+ * device), so a whole run of steps can be enqueued, or captured in a CUDA graph, and the
+ * host reads the state once at the end.  A solve that reports an error (MGS_ERANK, ...)
+ * sets done = 2 and status to that code and leaves x unchanged.
+ */
+#define MGS_NEWTON_HISTORY 64
+typedef struct {
+  int32_t done;       /* 0 running, 1 converged, 2 stopped by a solve status */
+  int32_t iterations; /* steps taken */
+  int32_t status;     /* the solve status that stopped the run (done == 2) */
+  int32_t reserved;
+  double f_norm[MGS_NEWTON_HISTORY];  /* ||F(x_i)||_inf, as passed to step i */
+  double dx_norm[MGS_NEWTON_HISTORY]; /* ||x_{i+1} - x_i||_inf */
+  double x_norm[MGS_NEWTON_HISTORY];  /* ||x_{i+1}||_inf */
+  double z[MGS_NEWTON_HISTORY];       /* residual of the linearised problem of step i */
+} mgs_newton_state;
+
+/* Workspace bytes of newton_step_* (the solve's workspace plus the step s); 0 when
+ * unsupported. */
+size_t newton_workspace_bytes(int limbs, int m, int n);
+
+/*
+ * One gated Newton step (see above).
+ *   J          in: m x n Jacobian (ldj >= m), layout of A in ls_solve_*; out: overwritten (Q)
+ *   F          in: F(x), m elements; out: overwritten (the linearised residual)
+ *   x          in/out: n elements, 16-byte aligned
+ *   tol        relative stopping tolerance on the step (>= 0)
+ *   dev_state  device mgs_newton_state, 16-byte aligned, zeroed by the caller before the
+ *              first step of a run
+ *   workspace  newton_workspace_bytes(limbs, m, n) bytes of device memory
+ *   dev_status device int32: the status of this step's solve (reset by each step)
+ * Host returns: MGS_OK, MGS_EINVAL, MGS_ENOSPACE or MGS_ECUDA.
+ */
+int newton_step_d(double* J, int ldj, double* F, double* x, int m, int n, double tol, mgs_newton_state* dev_state,
+                  void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+int newton_step_dd(double* J, int ldj, double* F, double* x, int m, int n, double tol, mgs_newton_state* dev_state,
+                   void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+int newton_step_qd(double* J, int ldj, double* F, double* x, int m, int n, double tol, mgs_newton_state* dev_state,
+                   void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

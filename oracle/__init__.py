@@ -72,6 +72,7 @@ class Oracle:
             "oracle_ls_solve": (i, [i, vp, vp, vp, vp, vp, i, i, i, i]),
             "oracle_qr": (i, [i, vp, vp, i, i, i, i]),
             "oracle_matvec": (None, [i, vp, i, i, i, vp, i, vp]),
+            "oracle_matvec_conjT": (None, [i, vp, i, i, i, vp, i, vp]),
             "oracle_qr_error": (d, [i, vp, i, vp, i, vp, i, i, i, vp]),
             "oracle_orth_error": (d, [i, vp, i, i, i]),
             "oracle_residual": (d, [i, vp, i, vp, vp, i, i, i, vp]),
@@ -173,6 +174,16 @@ class Oracle:
         self.lib.oracle_matvec(L, _ptr(A), m, n, m, _ptr(x), Lout, _ptr(b))
         return b
 
+    def matvec_conjT(self, A: np.ndarray, v: np.ndarray, Lout: int | None = None):
+        """A^H v, each entry exact then rounded to Lout limbs (v: (m, 2, L))."""
+        n, m, _, L = A.shape
+        Lout = Lout or L
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros((n, 2, Lout))
+        self.lib.oracle_matvec_conjT(L, _ptr(A), m, n, m, _ptr(v), Lout, _ptr(out))
+        return out
+
     def qr_error(self, A, Q, R):
         """Eq. (2): max_ij |a_ij - (QR)_ij| (exact residual, modulus in double)."""
         n, m, _, L = A.shape
@@ -210,6 +221,18 @@ class Oracle:
         d = self.lib.oracle_max_abs_diff(La, _ptr(a), Lb, _ptr(b), ca, ctypes.byref(bmax))
         return float(d), float(bmax.value)
 
+
+    def newton_step(self, J, F, x):
+        """One Newton corrector step (Section 7) on the caller's Jacobian J and residual F:
+        s = argmin ||F - J s|| by ls_solve, then x - s per real part.  Returns
+        (x_new, s, z, status)."""
+        r = self.ls_solve(J, F)
+        L = x.shape[-1]
+        xn = np.empty_like(x)
+        for j in range(x.shape[0]):
+            for p in range(2):
+                xn[j, p] = self.sub(L, x[j, p], r["x"][j, p])
+        return xn, r["x"], r["z"], r["status"]
 
     def ls_adjoint(self, A, b, G):
         """Gradients (grad_A, grad_b) of a real loss with dL/dx = G (PyTorch's complex

@@ -615,6 +615,35 @@ EXPORT void oracle_matvec(int Lin, const double *A, int m, int n, int lda, const
 }
 
 /*
+ * out = A^H v (n entries): out_j = sum_i conj(a_ij) v_i, each sum exact, then rounded to
+ * Lout limbs.  conj(a) v = (ar vr + ai vi) + i (ar vi - ai vr).  With v a column of Q this
+ * is a column of Q^H Q (the orthogonality of Section 3); with v = b - A x it is the
+ * normal-equations residual of the least-squares solution.
+ */
+EXPORT void oracle_matvec_conjT(int Lin, const double *A, int m, int n, int lda, const double *v, int Lout,
+                                double *out) {
+  static __thread xp Er, Ei;
+  for (int j = 0; j < n; ++j) {
+    Er.n = 0;
+    Ei.n = 0;
+    for (int i = 0; i < m; ++i) {
+      cx a = cx_load(ELEM(A, i, j, lda, Lin), Lin);
+      cx w = cx_load(v + (size_t)i * 2 * Lin, Lin);
+      xp_add_prod(&Er, &a.re, &w.re, Lin, 1.0);
+      xp_add_prod(&Er, &a.im, &w.im, Lin, 1.0);
+      xp_add_prod(&Ei, &a.re, &w.im, Lin, 1.0);
+      xp_add_prod(&Ei, &a.im, &w.re, Lin, -1.0);
+      if (Er.n > 256) xp_compress(&Er);
+      if (Ei.n > 256) xp_compress(&Ei);
+    }
+    cx z;
+    z.re = xp_round(&Er, Lout);
+    z.im = xp_round(&Ei, Lout);
+    cx_store(out + (size_t)j * 2 * Lout, &z, Lout);
+  }
+}
+
+/*
  * Eq. (2): e = max_{i,j} | a_ij - sum_l q_il r_lj | (complex modulus), the inner sum and
  * the difference evaluated exactly, the modulus in double.  A is the ORIGINAL matrix,
  * Q (m x n) and R (n x n, upper) the computed factors; all carry L limbs.

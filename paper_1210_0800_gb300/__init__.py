@@ -26,3 +26,4 @@ from ._binding import (  # noqa: F401
     mgs_workspace_bytes,
 )
 from .autograd import LeastSquares, lstsq  # noqa: F401,E402
+from .newton import NewtonState, newton_corrector, newton_step  # noqa: F401,E402

@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "MGS_OK", 1: "MGS_EINVAL", 2: "MGS_ERANK", 3: "MGS_ENONFINITE
 EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_workspace_bytes",
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
            "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
-           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched", "mgs_plan_query"]
+           "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched", "mgs_plan_query",
+           "newton_workspace_bytes", "newton_step_d", "newton_step_dd", "newton_step_qd"]
 
 
 class MgsTune(ctypes.Structure):
@@ -55,6 +56,11 @@ def load(path: str | None = None):
     lib.mgs_last_cuda_error.restype = i
     lib.mgs_workspace_bytes.restype = sz
     lib.mgs_workspace_bytes.argtypes = [i, i, i, i]
+    lib.newton_workspace_bytes.restype = sz
+    lib.newton_workspace_bytes.argtypes = [i, i, i]
+    for name in ("newton_step_d", "newton_step_dd", "newton_step_qd"):
+        getattr(lib, name).restype = i
+        getattr(lib, name).argtypes = [dp, i, dp, dp, i, i, ctypes.c_double, vp, vp, sz, vp, vp]
     lib.mgs_plan_query.restype = i
     lib.mgs_plan_query.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int)]
     qr_args = [dp, i, dp, i, i, i, vp, sz, vp, vp]

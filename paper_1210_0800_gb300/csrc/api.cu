@@ -4,6 +4,9 @@
 
 #include <cstdint>
 #include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "../../include/mgs_ddqd.h"
 #include "launch.cuh"
@@ -21,6 +24,12 @@ int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaS
 }
 int cluster_capacity(int L, int cl, size_t smem) {
   return L == 1 ? cluster_capacity_d(cl, smem) : L == 2 ? cluster_capacity_dd(cl, smem) : cluster_capacity_qd(cl, smem);
+}
+int blocks_per_sm_d(int kind, size_t smem);
+int blocks_per_sm_dd(int kind, size_t smem);
+int blocks_per_sm_qd(int kind, size_t smem);
+int grid_capacity(int L, int kind, size_t smem) {
+  return L == 1 ? blocks_per_sm_d(kind, smem) : L == 2 ? blocks_per_sm_dd(kind, smem) : blocks_per_sm_qd(kind, smem);
 }
 }  // namespace mgs
 
@@ -59,7 +68,7 @@ int device_sms() {
 }
 
 // Rows per CTA about 64; as many column groups as SMs allow; every row block non-empty.
-bool make_plan(int L, int m, int n, int aug, Plan& pl) {
+bool compute_plan(int L, int m, int n, int aug, int want, int h0, Plan& pl) {
   if ((L != 1 && L != 2 && L != 4) || n < 1 || m < n) return false;
   const int sms = device_sms();
   if (sms <= 0) return false;
@@ -73,11 +82,7 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   // schedule on hardware clusters for complex double and double-double (where the
   // per-step latency is a large share of a step), the grid-barrier kernel where hardware
   // clusters cannot be formed and for quad double (where the FP64 throughput decides)
-  const char* kenv = std::getenv("MGS_KERNEL");
-  const int want = !kenv ? -1 : kenv[0] == 'g' && kenv[1] == 'r' && kenv[2] == 'i' ? 0 : kenv[0] == 'c' ? 1 : 2;
-  const char* henv = std::getenv("MGS_ROWS");  // rows per row block (tuning override)
-  int h = henv ? std::atoi(henv) : 64;
-  if (h < 8 || h > 1024) h = 64;
+  int h = h0;
   const size_t pad = one_cta_per_sm_smem();
   auto padded = [&](size_t v) { return (pad > v && pad <= kMaxSmem) ? pad : v; };
   for (;;) {
@@ -108,6 +113,7 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
     const size_t bs = mgs::backsub_smem_bytes(L);
     if (bs > smem) smem = bs;
     if (smem <= kMaxSmem) {
+      if (kind != 1 && mgs::grid_capacity(L, kind, padded(smem)) * sms < Br * Bc) return false;
       pl.Br = Br;
       pl.Bc = Bc;
       pl.h = h;
@@ -149,10 +155,46 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   return true;
 }
 
+// The plan for (device, sizes, kernel choice), computed once: it queries occupancy, which
+// costs far more host time than a launch.
+bool make_plan(int L, int m, int n, int aug, Plan& pl) {
+  struct Entry {
+    int dev, L, m, n, aug, want, h;
+    Plan pl;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  // MGS_KERNEL = grid | cluster | group, MGS_ROWS = h: overrides, read at every call
+  const char* kenv = std::getenv("MGS_KERNEL");
+  const int want = !kenv                          ? -1
+                   : std::strcmp(kenv, "grid") == 0    ? 0
+                   : std::strcmp(kenv, "cluster") == 0 ? 1
+                   : std::strcmp(kenv, "group") == 0   ? 2
+                                                       : -1;
+  const char* henv = std::getenv("MGS_ROWS");
+  int h = henv ? std::atoi(henv) : 64;
+  if (h < 8 || h > 1024) h = 64;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (const Entry& e : cache)
+      if (e.dev == dev && e.L == L && e.m == m && e.n == n && e.aug == aug && e.want == want && e.h == h) {
+        pl = e.pl;
+        return true;
+      }
+  }
+  if (!compute_plan(L, m, n, aug, want, h, pl)) return false;
+  std::lock_guard<std::mutex> g(mu);
+  if (cache.size() >= 256) cache.clear();
+  cache.push_back(Entry{dev, L, m, n, aug, want, h, pl});
+  return true;
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, double* z, int m, int n, void* ws,
-        size_t ws_bytes, int32_t* dev_status, void* stream, int aug) {
+        size_t ws_bytes, int32_t* dev_status, void* stream, int aug, const int32_t* skip = nullptr) {
   if (!A || !dev_status || !ws) return MGS_EINVAL;
   if (aug && (!b || !x)) return MGS_EINVAL;
   if (!aug && !R) return MGS_EINVAL;
@@ -201,6 +243,7 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   pr.one = 1.0;
   pr.nzero = -0.0;
   pr.timeout_ns = kTimeoutNs;
+  pr.skip = skip;
 #if defined(MGS_TRACE) && MGS_TRACE
   pr.trace = reinterpret_cast<unsigned long long*>(wb + pl.off_T);
 #else
@@ -227,6 +270,11 @@ namespace mgs {
 // Lets the other translation units of the library record a CUDA error for
 // mgs_last_cuda_error().
 void set_last_cuda_error(int code) { g_last_cuda = code; }
+// The least-squares solve of ls_solve_*, doing nothing when *skip != 0 at launch time.
+int ls_solve_gated(int L, double* A, int lda, double* b, double* x, double* z, int m, int n, void* ws,
+                   size_t ws_bytes, int32_t* dev_status, void* stream, const int32_t* skip) {
+  return run(L, A, lda, b, x, nullptr, 0, z, m, n, ws, ws_bytes, dev_status, stream, 1, skip);
+}
 }  // namespace mgs
 
 extern "C" {

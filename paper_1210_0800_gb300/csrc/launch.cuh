@@ -1,41 +1,79 @@
-// Cooperative launch of the persistent MGS kernel (all CTAs co-resident: the kernel's
-// grid barriers and pivot flags rely on it).
+// Launch of the persistent single-system MGS kernels.  All CTAs must be co-resident (the
+// kernels' barriers and pivot flags rely on it): the plan checks residency once per
+// layout (blocks_per_sm, max_active_clusters), the launches are cooperative where the
+// driver allows it, and every wait in the kernels is bounded.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
 
 #include "mgs_cluster.cuh"
 #include "mgs_kernel.cuh"
 
 namespace mgs {
 
+// Raises a kernel's dynamic shared-memory limit on the current device once (again only
+// when more is asked for), so that a launch costs no attribute call.
+inline cudaError_t ensure_smem(const void* kern, size_t smem) {
+  struct Entry {
+    const void* kern;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  for (Entry& d : done)
+    if (d.kern == kern && d.dev == dev) {
+      if (d.bytes >= smem) return cudaSuccess;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) d.bytes = smem;
+      return e;
+    }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.push_back(Entry{kern, dev, smem});
+  return e;
+}
+
 // kind 0: mgs_ls_kernel (a grid barrier per step); kind 2: the cluster schedule with
 // software groups (mgs_cluster_kernel<Ar, false>).
 template <class Ar>
-int launch_kernel(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
-  auto kern = kind == 2 ? mgs_cluster_kernel<Ar, false> : mgs_ls_kernel<Ar>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
+const void* grid_kernel(int kind) {
+  return kind == 2 ? (const void*)mgs_cluster_kernel<Ar, false> : (const void*)mgs_ls_kernel<Ar>;
+}
+
+// Resident CTAs per SM of a plain-grid kernel with `smem` bytes of shared memory.
+template <class Ar>
+int blocks_per_sm(int kind, size_t smem) {
+  const void* kern = grid_kernel<Ar>(kind);
+  if (ensure_smem(kern, smem) != cudaSuccess) return 0;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) return 0;
+  return per_sm;
+}
+
+template <class Ar>
+int launch_kernel(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
+  const void* kern = grid_kernel<Ar>(kind);
+  cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return (int)e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (per_sm * sms < grid) return (int)cudaErrorCooperativeLaunchTooLarge;
   Params copy = pr;
   void* args[] = {&copy};
-  e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem, stream);
-  return (int)e;
+  return (int)cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), args, smem, stream);
 }
 
 // Cluster variant: clusters of `cl` CTAs (the row blocks of a column group).  Launched
 // cooperatively when the driver accepts cooperative cluster launches, otherwise as a plain
-// cluster launch after checking that every cluster can be resident at once.
+// cluster launch (the plan has checked that every cluster can be resident at once).
 template <class Ar>
 int launch_cluster_kernel(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
   auto kern = mgs_cluster_kernel<Ar, true>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem((const void*)kern, smem);
   if (e != cudaSuccess) return (int)e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -50,12 +88,15 @@ int launch_cluster_kernel(const Params& pr, int grid, int cl, size_t smem, cudaS
   attrs[1].id = cudaLaunchAttributeCooperative;
   attrs[1].val.cooperative = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  int max_clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
-  if (e != cudaSuccess) return (int)e;
-  if (max_clusters * cl < grid) return (int)cudaErrorCooperativeLaunchTooLarge;
   Params copy = pr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return (int)e;
+  if (cap != cudaStreamCaptureStatusNone) {
+    // inside a capture a refused launch would invalidate the graph: no second try
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, kern, copy);
+  }
   cfg.numAttrs = 2;
   e = cudaLaunchKernelEx(&cfg, kern, copy);
   if (e != cudaSuccess) {
@@ -70,7 +111,7 @@ int launch_cluster_kernel(const Params& pr, int grid, int cl, size_t smem, cudaS
 template <class Ar>
 int max_active_clusters(int cl, size_t smem) {
   auto kern = mgs_cluster_kernel<Ar, true>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (ensure_smem((const void*)kern, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl);
   cfg.blockDim = dim3(kThreads);
@@ -88,9 +129,10 @@ int max_active_clusters(int cl, size_t smem) {
 }
 
 int launch_d(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
-int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
-int cluster_capacity(int L, int cl, size_t smem);
 int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
 int launch_qd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
+int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
+int cluster_capacity(int L, int cl, size_t smem);
+int grid_capacity(int L, int kind, size_t smem);
 
 }  // namespace mgs

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
     for (int q = 0; q < L; ++q) dst[q] = d[q];
   };
 
+  if (pr.skip && *pr.skip) return;  // uniform over the grid: no barrier is entered
   MGS_TR_SMID();
   // ---------------------------------------------------------------- load the tile
   if (tid == 0) iflag[0] = 0;

@@ -69,6 +69,7 @@ struct Params {
   double one, nzero;
   long long timeout_ns;
   unsigned long long* trace;  // phase timestamps, (nc + 1) x grid x 8 (trace builds only)
+  const int* skip;            // when non-null and nonzero at launch the kernel does nothing
 };
 
 // Phase timestamps for performance analysis (compiled in with -DMGS_TRACE=1 only).
@@ -518,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     for (int q = 0; q < L; ++q) dst[q] = d[q];
   };
 
+  if (pr.skip && *pr.skip) return;  // uniform over the grid: no barrier is entered
   MGS_TR_SMID();
   // ---------------------------------------------------------------- load the tile
   if (tid == 0) iflag[0] = 0;

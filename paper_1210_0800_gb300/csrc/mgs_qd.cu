@@ -9,4 +9,5 @@ int launch_cluster_qd(const Params& pr, int grid, int cl, size_t smem, cudaStrea
   return launch_cluster_kernel<QD>(pr, grid, cl, smem, stream);
 }
 int cluster_capacity_qd(int cl, size_t smem) { return max_active_clusters<QD>(cl, smem); }
+int blocks_per_sm_qd(int kind, size_t smem) { return blocks_per_sm<QD>(kind, smem); }
 }  // namespace mgs

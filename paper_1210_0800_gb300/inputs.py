@@ -173,6 +173,19 @@ WORKLOADS = {
 }
 
 
+def workload_seed(name: str) -> int:
+    """Base seed of a named workload (its c0..c4 prefix); other names use c1's."""
+    key = name.split("_")[0]
+    return WORKLOADS[key]["seed"] if key in WORKLOADS else WORKLOADS["c1"]["seed"]
+
+
+def ragged_batch(L: int, batch: int, n_rng, e_rng, seed: int):
+    """A ragged batch of independent systems [(A, b_generic)], shapes from ragged_shapes."""
+    ms, ns = ragged_shapes(batch, seed, n_rng[0], n_rng[1], e_rng[0], e_rng[1])
+    return [(lambda s: (s[0], s[2]))(system(int(m), int(n), L, system_seed(seed, i))) for i, (m, n) in
+            enumerate(zip(ms, ns))]
+
+
 def system(m: int, n: int, L: int, seed: int, extreme: bool = False):
     """One least-squares system: (A, x_true, b_generic).
 

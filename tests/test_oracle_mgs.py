@@ -108,3 +108,84 @@ def test_dd_qd_agree(orc):
     r4 = orc.ls_solve(A4, b4)
     d, xm = orc.max_abs_diff(r2["x"], r4["x"])
     assert d / xm < 1e-27
+
+
+@pytest.mark.parametrize("L,Lout", [(1, 2), (2, 2), (2, 4), (4, 4)])
+def test_matvec_exact(orc, L, Lout):
+    """A x and A^H v against exact rational arithmetic: every entry within one rounding to
+    Lout limbs of the exact sum (the sums have cancellation: v = A x for some rows)."""
+    m, n = 7, 5
+    A = inputs.matrix_uniform(m, n, L, 6101)
+    x = inputs.system(m, n, L, 6102)[1]
+    v = inputs.system(m, n, L, 6103)[2]
+    v[3] = orc.matvec(A, x)[3]  # a row that is itself a combination of the columns
+    Aex = [[pins.cval(A[j, i]) for j in range(n)] for i in range(m)]
+    xex = [pins.cval(x[j]) for j in range(n)]
+    vex = [pins.cval(v[i]) for i in range(m)]
+    got = orc.matvec(A, x, Lout=Lout)
+    gotT = orc.matvec_conjT(A, v, Lout=Lout)
+    u = 2.0 ** (-53 * Lout)
+    for i in range(m):
+        want = (sum((pins.cmul(Aex[i][j], xex[j])[0] for j in range(n)), pins.F(0)),
+                sum((pins.cmul(Aex[i][j], xex[j])[1] for j in range(n)), pins.F(0)))
+        g = pins.cval(got[i])
+        for p in range(2):
+            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
+    for j in range(n):
+        want = pins.cdot([Aex[i][j] for i in range(m)], vex)
+        g = pins.cval(gotT[j])
+        for p in range(2):
+            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
+
+
+def test_matvec_conjT_gram(orc):
+    """Q^H q_j from the oracle's own MGS is a column of the identity up to O(kappa u)
+    (Section 3); a planted transposition (A^T instead of A^H) would leave the imaginary
+    cross terms at O(1)."""
+    A, _, _ = inputs.system(30, 12, 2, 6104)
+    Q, R, st = orc.qr(A.copy())
+    assert st == 0
+    for j in (0, 5, 11):
+        col = orc.matvec_conjT(Q, Q[j])
+        e = np.zeros_like(col)
+        e[j, 0, 0] = 1.0
+        d, _ = orc.max_abs_diff(col, e)
+        assert d < 1e-28
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_newton_linear_one_step(orc, L):
+    """For F(x) = A x - b the Newton step from any x0 lands on the least-squares solution:
+    x0 - argmin ||(A x0 - b) - A s|| = argmin ||b - A x|| (Section 7 with a linear system)."""
+    A, x0, b = inputs.system(14, 9, L, 6201)
+    ax = orc.matvec(A, x0, Lout=L)
+    F = np.empty_like(ax)
+    for i in range(14):
+        for p in range(2):
+            F[i, p] = orc.sub(L, ax[i, p], b[i, p])
+    x1, s, z, st = orc.newton_step(A.copy(), F, x0)
+    ref = orc.ls_solve(A.copy(), b.copy())
+    assert st == 0
+    d, xm = orc.max_abs_diff(x1, ref["x"])
+    assert d / xm < (1e-27 if L == 2 else 1e-58)
+
+
+def test_newton_quadratic_convergence(orc):
+    """On a quadratic system with a planted root the oracle's Newton iterates converge
+    quadratically (e_{k+1} <= C e_k^2) down to rounding level."""
+    import newton_problem as npb
+
+    m, n, L = 12, 8, 2
+    A, c, b, xs = npb.problem(orc, m, n, L, 6202)
+    x = xs.copy()
+    x[..., 0] += 1e-3 * inputs.uniform_pm1(6203, x[..., 0].size).reshape(x[..., 0].shape)
+    errs = []
+    for _ in range(6):
+        J, F = npb.evaluate(orc, A, c, b, x)
+        x, s, z, st = orc.newton_step(J, F, x)
+        assert st == 0
+        errs.append(orc.max_abs_diff(x, xs)[0])
+    assert errs[-1] < 1e-28
+    for e0, e1 in zip(errs, errs[1:]):
+        if e0 > 1e-14:
+            assert e1 <= 50 * e0 * e0, errs
