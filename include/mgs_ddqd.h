@@ -67,7 +67,7 @@ size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs);
 
 /*
  * How a single-system call of these sizes is laid out on the current device (no
- * counterpart in the paper; for tests and tuning).
+ * counterpart in the paper; for tests and tuning).  `out` has room for 5 ints.
  *   out[0] Br  row blocks (CTAs per column group), out[1] Bc  column groups,
  *   out[2] h   rows per row block, out[3] kernel:
  *     0  grid-barrier kernel: one grid-wide barrier per elimination step;
@@ -76,12 +76,16 @@ size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs);
  *        memory; Br <= 8);
  *     2  the same schedule on software groups (the Br CTAs meet at a counter in global
  *        memory and exchange partials through L2; every SM usable).
- *   The default is 1 for limbs 1 and 2 (0 where clusters cannot be formed) and 0 for
- *   limbs 4: measured on GB300, the cluster schedule hides the per-step latency that
- *   dominates the cheaper arithmetic, while quad double is bound by FP64 throughput.
+ *   The default is 1 for limbs 1 and 2 where the clusters fill at least 90 % of the SMs
+ *   a plain grid would use (else 0), and 0 for limbs 4: measured on GB300, the cluster
+ *   schedule hides the per-step latency that dominates the cheaper arithmetic, while quad
+ *   double, and layouts where clusters leave SMs idle, are bound by FP64 throughput.
  *   The environment variable MGS_KERNEL = grid | cluster | group, read at each call,
  *   forces a kernel (cluster falls back to grid where clusters cannot be formed);
- *   MGS_ROWS = h overrides the rows per row block (default 64).
+ *   out[4] threads per CTA: 128, or 256 where a CTA owns 16 or more columns (two warps
+ *          per SM sub-partition hide each other's FP64 latency in the long loops).
+ *   MGS_ROWS = h overrides the rows per row block (default 64); MGS_CTA_THREADS = 128 |
+ *   256 the threads per CTA.
  * Returns MGS_OK, MGS_EINVAL or MGS_ENOSPACE (no layout fits shared memory).
  */
 int mgs_plan_query(int limbs, int m, int n, int with_rhs, int* out);

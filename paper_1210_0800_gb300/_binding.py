@@ -227,12 +227,12 @@ def mgs_workspace_bytes(limbs: int, m: int, n: int, with_rhs: bool = True) -> in
 
 def mgs_plan_query(limbs: int, m: int, n: int, with_rhs: bool = True) -> dict:
     """Layout of a single-system call on the current device: row blocks Br, column groups
-    Bc, rows per block h and the kernel ("grid", "cluster" or "group")."""
-    out = (ctypes.c_int * 4)()
+    Bc, rows per block h, the kernel ("grid", "cluster" or "group") and threads per CTA."""
+    out = (ctypes.c_int * 5)()
     rc = load().mgs_plan_query(limbs, m, n, 1 if with_rhs else 0, out)
     if rc != 0:
         raise MGSError(rc, "mgs_plan_query")
-    return dict(Br=out[0], Bc=out[1], h=out[2], kernel=("grid", "cluster", "group")[out[3]])
+    return dict(Br=out[0], Bc=out[1], h=out[2], kernel=("grid", "cluster", "group")[out[3]], threads=out[4])
 
 
 # ----------------------------------------------------------------------------- batched

@@ -12,24 +12,25 @@
 #include "launch.cuh"
 
 namespace mgs {
-int launch_cluster_d(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
-int launch_cluster_dd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
-int launch_cluster_qd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
-int cluster_capacity_d(int cl, size_t smem);
-int cluster_capacity_dd(int cl, size_t smem);
-int cluster_capacity_qd(int cl, size_t smem);
-int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
-  return L == 1 ? launch_cluster_d(pr, grid, cl, smem, stream)
-                : L == 2 ? launch_cluster_dd(pr, grid, cl, smem, stream) : launch_cluster_qd(pr, grid, cl, smem, stream);
+int launch_cluster_d(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream);
+int launch_cluster_dd(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream);
+int launch_cluster_qd(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream);
+int cluster_capacity_d(int cl, int T, size_t smem);
+int cluster_capacity_dd(int cl, int T, size_t smem);
+int cluster_capacity_qd(int cl, int T, size_t smem);
+int launch_cluster(int L, const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream) {
+  return L == 1   ? launch_cluster_d(pr, grid, cl, T, smem, stream)
+         : L == 2 ? launch_cluster_dd(pr, grid, cl, T, smem, stream)
+                  : launch_cluster_qd(pr, grid, cl, T, smem, stream);
 }
-int cluster_capacity(int L, int cl, size_t smem) {
-  return L == 1 ? cluster_capacity_d(cl, smem) : L == 2 ? cluster_capacity_dd(cl, smem) : cluster_capacity_qd(cl, smem);
+int cluster_capacity(int L, int cl, int T, size_t smem) {
+  return L == 1 ? cluster_capacity_d(cl, T, smem) : L == 2 ? cluster_capacity_dd(cl, T, smem) : cluster_capacity_qd(cl, T, smem);
 }
-int blocks_per_sm_d(int kind, size_t smem);
-int blocks_per_sm_dd(int kind, size_t smem);
-int blocks_per_sm_qd(int kind, size_t smem);
-int grid_capacity(int L, int kind, size_t smem) {
-  return L == 1 ? blocks_per_sm_d(kind, smem) : L == 2 ? blocks_per_sm_dd(kind, smem) : blocks_per_sm_qd(kind, smem);
+int blocks_per_sm_d(int kind, int T, size_t smem);
+int blocks_per_sm_dd(int kind, int T, size_t smem);
+int blocks_per_sm_qd(int kind, int T, size_t smem);
+int grid_capacity(int L, int kind, int T, size_t smem) {
+  return L == 1 ? blocks_per_sm_d(kind, T, smem) : L == 2 ? blocks_per_sm_dd(kind, T, smem) : blocks_per_sm_qd(kind, T, smem);
 }
 }  // namespace mgs
 
@@ -45,6 +46,7 @@ struct Plan {
   int L, m, n, nc, aug;
   int Br, Bc, h, w;
   int kind;  // 0 grid barrier per step, 1 hardware clusters, 2 software groups
+  int T;     // threads per CTA (128 or 256)
   size_t smem;
   size_t off_sync, off_gsync, off_flags, off_P, off_V, off_Y, off_R, off_G, off_T, total, zero_bytes;
 };
@@ -68,7 +70,7 @@ int device_sms() {
 }
 
 // Rows per CTA about 64; as many column groups as SMs allow; every row block non-empty.
-bool compute_plan(int L, int m, int n, int aug, int want, int h0, Plan& pl) {
+bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, Plan& pl) {
   if ((L != 1 && L != 2 && L != 4) || n < 1 || m < n) return false;
   const int sms = device_sms();
   if (sms <= 0) return false;
@@ -80,8 +82,9 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, Plan& pl) {
   const int E = 2 * L;
   // MGS_KERNEL = grid | cluster | group overrides the default choice: the cluster
   // schedule on hardware clusters for complex double and double-double (where the
-  // per-step latency is a large share of a step), the grid-barrier kernel where hardware
-  // clusters cannot be formed and for quad double (where the FP64 throughput decides)
+  // per-step latency is a large share of a step) when the clusters fill at least 90 % of
+  // the SMs a plain grid would use; otherwise, and for quad double (where the FP64
+  // throughput decides), the grid-barrier kernel
   int h = h0;
   const size_t pad = one_cta_per_sm_smem();
   auto padded = [&](size_t v) { return (pad > v && pad <= kMaxSmem) ? pad : v; };
@@ -91,35 +94,40 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, Plan& pl) {
     const int Bc_grid = sms / Br < pl.nc ? sms / Br : pl.nc;
     if (Bc_grid < 1) return false;
     int kind = want < 0 ? (L <= 2 ? 1 : 0) : want, Bc = Bc_grid;
+    // 256 threads (two warps per sub-partition) where a CTA owns many columns: their
+    // long per-step loops then hide each other's FP64 latency
+    const int T = T0 ? T0 : ((pl.nc + Bc_grid - 1) / Bc_grid >= 16 ? 256 : 128);
     if (kind == 1) {
       // hardware clusters: as many column groups as clusters fit at once
       int cap = 0;
       if (Br <= 8) {
         for (int it = 0, Bt = Bc_grid; it < 3; ++it) {
           const int wt = (pl.nc + Bt - 1) / Bt;
-          cap = mgs::cluster_capacity(L, Br, padded(mgs::cluster_smem_bytes(L, h, wt)));
+          cap = mgs::cluster_capacity(L, Br, T, padded(mgs::cluster_smem_bytes(L, h, wt, T)));
           if (cap <= 0 || Bt <= cap) break;
           Bt = cap;
         }
       }
-      if (cap > 0) {
+      // by default only where the clusters occupy nearly as many SMs as a plain grid
+      if (cap > 0 && (want == 1 || 10 * cap >= 9 * Bc_grid)) {
         Bc = cap < Bc_grid ? cap : Bc_grid;
       } else {
         kind = 0;
       }
     }
     const int w = (pl.nc + Bc - 1) / Bc;
-    size_t smem = kind == 0 ? mgs::smem_bytes(L, h, w) : mgs::cluster_smem_bytes(L, h, w);
+    size_t smem = kind == 0 ? mgs::smem_bytes(L, h, w, T) : mgs::cluster_smem_bytes(L, h, w, T);
     const size_t bs = mgs::backsub_smem_bytes(L);
     if (bs > smem) smem = bs;
     if (smem <= kMaxSmem) {
-      if (kind != 1 && mgs::grid_capacity(L, kind, padded(smem)) * sms < Br * Bc) return false;
+      if (kind != 1 && mgs::grid_capacity(L, kind, T, padded(smem)) * sms < Br * Bc) return false;
       pl.Br = Br;
       pl.Bc = Bc;
       pl.h = h;
       pl.w = w;
       pl.smem = padded(smem);
       pl.kind = kind;
+      pl.T = T;
       break;
     }
     if (h <= 8) return false;
@@ -159,7 +167,7 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, Plan& pl) {
 // costs far more host time than a launch.
 bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   struct Entry {
-    int dev, L, m, n, aug, want, h;
+    int dev, L, m, n, aug, want, h, T;
     Plan pl;
   };
   static std::mutex mu;
@@ -174,20 +182,23 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   const char* henv = std::getenv("MGS_ROWS");
   int h = henv ? std::atoi(henv) : 64;
   if (h < 8 || h > 1024) h = 64;
+  const char* tenv = std::getenv("MGS_CTA_THREADS");  // 128 | 256 (default: by layout)
+  const int T = tenv && std::atoi(tenv) == 256 ? 256 : tenv && std::atoi(tenv) == 128 ? 128 : 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   {
     std::lock_guard<std::mutex> g(mu);
     for (const Entry& e : cache)
-      if (e.dev == dev && e.L == L && e.m == m && e.n == n && e.aug == aug && e.want == want && e.h == h) {
+      if (e.dev == dev && e.L == L && e.m == m && e.n == n && e.aug == aug && e.want == want && e.h == h &&
+          e.T == T) {
         pl = e.pl;
         return true;
       }
   }
-  if (!compute_plan(L, m, n, aug, want, h, pl)) return false;
+  if (!compute_plan(L, m, n, aug, want, h, T, pl)) return false;
   std::lock_guard<std::mutex> g(mu);
   if (cache.size() >= 256) cache.clear();
-  cache.push_back(Entry{dev, L, m, n, aug, want, h, pl});
+  cache.push_back(Entry{dev, L, m, n, aug, want, h, T, pl});
   return true;
 }
 
@@ -252,11 +263,11 @@ int run(int L, double* A, int lda, double* b, double* x, double* R, int ldr, dou
   const int grid = pl.Br * pl.Bc;
   int rc;
   if (pl.kind == 1)
-    rc = mgs::launch_cluster(L, pr, grid, pl.Br, pl.smem, st);
+    rc = mgs::launch_cluster(L, pr, grid, pl.Br, pl.T, pl.smem, st);
   else
-    rc = (L == 1) ? mgs::launch_d(pr, grid, pl.smem, st, pl.kind)
-         : (L == 2) ? mgs::launch_dd(pr, grid, pl.smem, st, pl.kind)
-                    : mgs::launch_qd(pr, grid, pl.smem, st, pl.kind);
+    rc = (L == 1) ? mgs::launch_d(pr, grid, pl.T, pl.smem, st, pl.kind)
+         : (L == 2) ? mgs::launch_dd(pr, grid, pl.T, pl.smem, st, pl.kind)
+                    : mgs::launch_qd(pr, grid, pl.T, pl.smem, st, pl.kind);
   if (rc != 0) {
     g_last_cuda = rc;
     return MGS_ECUDA;
@@ -323,6 +334,7 @@ int mgs_plan_query(int limbs, int m, int n, int with_rhs, int* out) {
   out[1] = pl.Bc;
   out[2] = pl.h;
   out[3] = pl.kind;
+  out[4] = pl.T;
   return MGS_OK;
 }
 

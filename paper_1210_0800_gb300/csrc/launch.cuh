@@ -41,43 +41,48 @@ inline cudaError_t ensure_smem(const void* kern, size_t smem) {
 }
 
 // kind 0: mgs_ls_kernel (a grid barrier per step); kind 2: the cluster schedule with
-// software groups (mgs_cluster_kernel<Ar, false>).
+// software groups (mgs_cluster_kernel<Ar, false>); T threads per CTA (128 or 256).
 template <class Ar>
-const void* grid_kernel(int kind) {
-  return kind == 2 ? (const void*)mgs_cluster_kernel<Ar, false> : (const void*)mgs_ls_kernel<Ar>;
+const void* grid_kernel(int kind, int T) {
+  if (T == 256) return kind == 2 ? (const void*)mgs_cluster_kernel<Ar, false, 256> : (const void*)mgs_ls_kernel<Ar, 256>;
+  return kind == 2 ? (const void*)mgs_cluster_kernel<Ar, false, 128> : (const void*)mgs_ls_kernel<Ar, 128>;
+}
+template <class Ar>
+const void* cluster_kernel(int T) {
+  return T == 256 ? (const void*)mgs_cluster_kernel<Ar, true, 256> : (const void*)mgs_cluster_kernel<Ar, true, 128>;
 }
 
 // Resident CTAs per SM of a plain-grid kernel with `smem` bytes of shared memory.
 template <class Ar>
-int blocks_per_sm(int kind, size_t smem) {
-  const void* kern = grid_kernel<Ar>(kind);
+int blocks_per_sm(int kind, int T, size_t smem) {
+  const void* kern = grid_kernel<Ar>(kind, T);
   if (ensure_smem(kern, smem) != cudaSuccess) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem) != cudaSuccess) return 0;
   return per_sm;
 }
 
 template <class Ar>
-int launch_kernel(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
-  const void* kern = grid_kernel<Ar>(kind);
+int launch_kernel(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind) {
+  const void* kern = grid_kernel<Ar>(kind, T);
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return (int)e;
   Params copy = pr;
   void* args[] = {&copy};
-  return (int)cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), args, smem, stream);
+  return (int)cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(T), args, smem, stream);
 }
 
 // Cluster variant: clusters of `cl` CTAs (the row blocks of a column group).  Launched
 // cooperatively when the driver accepts cooperative cluster launches, otherwise as a plain
 // cluster launch (the plan has checked that every cluster can be resident at once).
 template <class Ar>
-int launch_cluster_kernel(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
-  auto kern = mgs_cluster_kernel<Ar, true>;
-  cudaError_t e = ensure_smem((const void*)kern, smem);
+int launch_cluster_kernel(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream) {
+  const void* kern = cluster_kernel<Ar>(T);
+  cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return (int)e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(T);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attrs[2];
@@ -89,32 +94,33 @@ int launch_cluster_kernel(const Params& pr, int grid, int cl, size_t smem, cudaS
   attrs[1].val.cooperative = 1;
   cfg.attrs = attrs;
   Params copy = pr;
+  void* args[] = {&copy};
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   e = cudaStreamIsCapturing(stream, &cap);
   if (e != cudaSuccess) return (int)e;
   if (cap != cudaStreamCaptureStatusNone) {
     // inside a capture a refused launch would invalidate the graph: no second try
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, kern, copy);
+    return (int)cudaLaunchKernelExC(&cfg, kern, args);
   }
   cfg.numAttrs = 2;
-  e = cudaLaunchKernelEx(&cfg, kern, copy);
+  e = cudaLaunchKernelExC(&cfg, kern, args);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, copy);
+    e = cudaLaunchKernelExC(&cfg, kern, args);
   }
   return (int)e;
 }
 
 // How many clusters of `cl` CTAs with `smem` bytes each can be resident at once.
 template <class Ar>
-int max_active_clusters(int cl, size_t smem) {
-  auto kern = mgs_cluster_kernel<Ar, true>;
-  if (ensure_smem((const void*)kern, smem) != cudaSuccess) return 0;
+int max_active_clusters(int cl, int T, size_t smem) {
+  const void* kern = cluster_kernel<Ar>(T);
+  if (ensure_smem(kern, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(T);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeClusterDimension;
@@ -128,11 +134,11 @@ int max_active_clusters(int cl, size_t smem) {
   return n;
 }
 
-int launch_d(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
-int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
-int launch_qd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind);
-int launch_cluster(int L, const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream);
-int cluster_capacity(int L, int cl, size_t smem);
-int grid_capacity(int L, int kind, size_t smem);
+int launch_d(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind);
+int launch_dd(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind);
+int launch_qd(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind);
+int launch_cluster(int L, const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream);
+int cluster_capacity(int L, int cl, int T, size_t smem);
+int grid_capacity(int L, int kind, int T, size_t smem);
 
 }  // namespace mgs

@@ -65,13 +65,13 @@ __host__ __device__ inline size_t group_partials_doubles(int L, int Br, int Bc, 
 
 // Extra shared memory of the cluster kernel on top of smem_bytes(): B partials (two
 // buffers of w + 1 items x 2 parts), A partials (2 items x 2 parts), reduced values.
-__host__ __device__ inline size_t cluster_smem_bytes(int L, int h, int w) {
-  return smem_bytes(L, h, w) +
+__host__ __device__ inline size_t cluster_smem_bytes(int L, int h, int w, int T) {
+  return smem_bytes(L, h, w, T) +
          sizeof(double) * (2 * (size_t)(w + 1) * 2 * L + (size_t)2 * 2 * L + (size_t)(w + 2) * 2 * L) + 64;
 }
 
-template <class Ar, bool HW>
-__global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
+template <class Ar, bool HW, int T>
+__global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
   namespace cg = cooperative_groups;
   constexpr int L = Ar::L, E = 2 * L;
   using elem = typename Ar::elem;
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
   double* coef = piv + (size_t)2 * E * h;    // w * E
   double* gkk = coef + (size_t)w * E;        // E
   double* scal = gkk + E;                    // 4 * E
-  double* redb = scal + 4 * E;               // kThreads * L
-  double* pbuf = redb + (size_t)kThreads * L;        // 2 x (w + 1) x 2 x PACC
+  double* redb = scal + 4 * E;               // T * L
+  double* pbuf = redb + (size_t)T * L;        // 2 x (w + 1) x 2 x PACC
   double* pabuf = pbuf + 2 * (size_t)(w + 1) * 2 * PACC;  // 2 x 2 x PACC
   double* gres = pabuf + 2 * 2 * PACC;               // (w + 2) x E reduced values
   // HW = false: the partial buffers live in global memory, CTA-major within a group so
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
   __syncthreads();
   {
     bool bad = false;
-    for (int idx = tid; idx < w * h; idx += kThreads) {
+    for (int idx = tid; idx < w * h; idx += T) {
       const int s = idx / h, l = idx % h;
       elem e;
       if (l < hr) {
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
     }
     if (bad) iflag[0] = 1;
   }
-  for (int l = tid; l < h; l += kThreads) {
+  for (int l = tid; l < h; l += T) {
     elem e;
     if (l < hr) {
       e = g_load<Ar>(colptr(0, r0 + l));
@@ -169,9 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
   // memory; results at out[(it * 2 + part) * PACC].
   auto item_partials = [&](const double* pivbuf, int nit, auto slot_of, double* out) {
     const int pairs = 2 * nit;
-    int C = kThreads / pairs;
+    int C = T / pairs;
     C = max(1, min(C, max(hr, 1)));
-    const int per_round = kThreads / C;
+    const int per_round = T / C;
     for (int base = 0; base < pairs; base += per_round) {
       const int job = tid / C, ch = tid % C, pi = base + job;
       const bool act = job < per_round && pi < pairs;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
   auto cluster_reduce = [&](double* buf, int nit, auto is_norm) {
     const int BrP = pow2_ceil(Br);
     const int jobs = nit * 2 * BrP;
-    for (int base = 0; base < jobs; base += kThreads) {
+    for (int base = 0; base < jobs; base += T) {
       const int job = base + tid;
       const int it = job / (2 * BrP), rem = job % (2 * BrP);
       const int part = rem / BrP, pp = rem % BrP;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
 
   auto coef_of = [&](int s, const real& G, bool ok, const double* gsrc) {
     const double invG = Ar::inv_lead(G);
-    for (int t = tid; t < 2; t += kThreads) {
+    for (int t = tid; t < 2; t += T) {
       const int part = t;
       const elem g = sm_load_part<Ar>(gsrc, 1, 0, part);
       elem cc = g;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
       elem cc;
 #pragma unroll
       for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s1 * E + q];
-      for (int t = tid; t < 2 * hr; t += kThreads) {
+      for (int t = tid; t < 2 * hr; t += T) {
         const int l = t >> 1, part = t & 1;
         elem y = sm_load_part<Ar>(ts, h, l, part);
         Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
@@ -308,13 +308,13 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
           pnxt[(part * L + q) * h + l] = y.v[part * L + q];
         }
       }
-      for (int l = hr + tid; l < h; l += kThreads) {
+      for (int l = hr + tid; l < h; l += T) {
 #pragma unroll
         for (int q = 0; q < E; ++q) pnxt[q * h + l] = 0.0;
       }
       __syncthreads();
       double* vdst = pr.V + ((size_t)(k + 1) * Br + p) * h * E;
-      for (int l = tid; l < h; l += kThreads) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
+      for (int l = tid; l < h; l += T) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
       }
       if (pr.aug) {
         const double* ts = tile + (size_t)(k / Bc) * E * h;
-        for (int l = tid; l < hr; l += kThreads) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
+        for (int l = tid; l < hr; l += T) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
         break;
       }
     }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
     {
       const double invG = Ar::inv_lead(G);
       const int ib = norm_here ? 1 : 0;
-      for (int t = tid; t < 2 * nb; t += kThreads) {
+      for (int t = tid; t < 2 * nb; t += T) {
         const int it = t >> 1, part = t & 1, s = sb + it;
         const elem g = sm_load_part<Ar>(gres + (size_t)(it + ib) * E, 1, 0, part);
         elem cc = g;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
     MGS_TR(k, 3);
     // coefficients of row k to R (row k) and Y (column b); scaled by r_kk at the end
     if (p == 0) {
-      for (int t = tid; t < nact; t += kThreads) {
+      for (int t = tid; t < nact; t += T) {
         const int s = first + t, j = col_of(s);
         elem cc;
 #pragma unroll
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
     // update the columns of B
     if (nb > 0 && hr > 0) {
       const int tot = nb * hr * 2;
-      for (int idx = tid; idx < tot; idx += kThreads) {
+      for (int idx = tid; idx < tot; idx += T) {
         const int part = idx & 1, rest = idx >> 1;
         const int s = sb + rest / hr, l = rest % hr;
         double* ts = tile + (size_t)s * E * h;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
       if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
       __syncthreads();
       const double* vsrc = pr.V + ((size_t)(k + 1) * Br + p) * h * E;
-      for (int l = tid; l < h; l += kThreads) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+      for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
     }
     __syncthreads();
     MGS_TR(k, 5);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_cluster_kernel(Params pr) {
   group_sync();
   grid_barrier(pr, epoch);
   MGS_TR(nc, 0);
-  mgs_epilogue<Ar>(pr, epoch, sm, p, c);
+  mgs_epilogue<Ar, T>(pr, epoch, sm, p, c);
 }
 
 }  // namespace mgs

@@ -2,12 +2,12 @@
 #include "launch.cuh"
 
 namespace mgs {
-int launch_d(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
-  return launch_kernel<D>(pr, grid, smem, stream, kind);
+int launch_d(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind) {
+  return launch_kernel<D>(pr, grid, T, smem, stream, kind);
 }
-int launch_cluster_d(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
-  return launch_cluster_kernel<D>(pr, grid, cl, smem, stream);
+int launch_cluster_d(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream) {
+  return launch_cluster_kernel<D>(pr, grid, cl, T, smem, stream);
 }
-int cluster_capacity_d(int cl, size_t smem) { return max_active_clusters<D>(cl, smem); }
-int blocks_per_sm_d(int kind, size_t smem) { return blocks_per_sm<D>(kind, smem); }
+int cluster_capacity_d(int cl, int T, size_t smem) { return max_active_clusters<D>(cl, T, smem); }
+int blocks_per_sm_d(int kind, int T, size_t smem) { return blocks_per_sm<D>(kind, T, smem); }
 }  // namespace mgs

@@ -2,12 +2,12 @@
 #include "launch.cuh"
 
 namespace mgs {
-int launch_dd(const Params& pr, int grid, size_t smem, cudaStream_t stream, int kind) {
-  return launch_kernel<DD>(pr, grid, smem, stream, kind);
+int launch_dd(const Params& pr, int grid, int T, size_t smem, cudaStream_t stream, int kind) {
+  return launch_kernel<DD>(pr, grid, T, smem, stream, kind);
 }
-int launch_cluster_dd(const Params& pr, int grid, int cl, size_t smem, cudaStream_t stream) {
-  return launch_cluster_kernel<DD>(pr, grid, cl, smem, stream);
+int launch_cluster_dd(const Params& pr, int grid, int cl, int T, size_t smem, cudaStream_t stream) {
+  return launch_cluster_kernel<DD>(pr, grid, cl, T, smem, stream);
 }
-int cluster_capacity_dd(int cl, size_t smem) { return max_active_clusters<DD>(cl, smem); }
-int blocks_per_sm_dd(int kind, size_t smem) { return blocks_per_sm<DD>(kind, smem); }
+int cluster_capacity_dd(int cl, int T, size_t smem) { return max_active_clusters<DD>(cl, T, smem); }
+int blocks_per_sm_dd(int kind, int T, size_t smem) { return blocks_per_sm<DD>(kind, T, smem); }
 }  // namespace mgs

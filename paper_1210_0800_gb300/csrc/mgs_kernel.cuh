@@ -39,10 +39,8 @@ namespace mgs {
 
 enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ERANK = 2, ST_ENONFINITE = 3, ST_ETIMEOUT = 4 };
 
-#ifndef MGS_THREADS
-#define MGS_THREADS 128
-#endif
-constexpr int kThreads = MGS_THREADS;
+// Threads per CTA of the single-system kernels: 128 (one warp per SM sub-partition) or 256
+// (two), a template parameter chosen per layout by the plan.
 
 struct Params {
   double* A;  // m x n, column-major by element, leading dimension lda (elements); Q on exit
@@ -247,12 +245,12 @@ __device__ __forceinline__ int pow2_floor(int v) { return v <= 1 ? 1 : 1 << (31 
 __device__ __forceinline__ int pow2_ceil(int v) { return v <= 1 ? 1 : 1 << (32 - __clz(v - 1)); }
 
 // Shared-memory footprint (bytes) of one CTA.
-__host__ __device__ inline size_t smem_bytes(int L, int h, int w) {
+__host__ __device__ inline size_t smem_bytes(int L, int h, int w, int T) {
   const size_t E = 2 * (size_t)L;
   return sizeof(double) * ((size_t)(w + 2) * E * h  // tile + two pivot buffers
                            + (size_t)(w + 1) * E     // coefficients + pivot norm
                            + 4 * E                   // scalars
-                           + (size_t)kThreads * L)   // partial-sum reduction tree
+                           + (size_t)T * L)          // partial-sum reduction tree
          + 16 * sizeof(int);
 }
 
@@ -266,7 +264,7 @@ __host__ __device__ inline size_t backsub_smem_bytes(int L) {
 // Normalisation (Q = a_k / r_kk from the CTA's resident tile, R = c r_kk), then the
 // back substitution; shared by the single-system kernels.  The tile layout is the one
 // both kernels keep in shared memory: slot s of column c + s Bc, limb planes of h rows.
-template <class Ar>
+template <class Ar, int T>
 __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, double* sm, int p, int c) {
   constexpr int L = Ar::L, E = 2 * L;
   using elem = typename Ar::elem;
@@ -294,8 +292,8 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     for (int q = 0; q < L; ++q) dst[q] = d[q];
   };
   // ---------------------------------------------------------------- normalisation
-  const int nthreads = gridDim.x * kThreads;
-  const int gtid = blockIdx.x * kThreads + tid;
+  const int nthreads = gridDim.x * T;
+  const int gtid = blockIdx.x * T + tid;
   // (E1) r_kk = sqrt(G_kk) and 1 / r_kk for every column, spread over all threads
   for (int k = gtid; k < nc; k += nthreads) {
     const real G = ld_real(pr.Gd + (size_t)k * L);
@@ -312,7 +310,7 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     const int wq = (nq - c + Bc - 1) / Bc;
     if (wq > 0 && hr > 0) {
       const int tot = wq * hr * 2;
-      for (int idx = tid; idx < tot; idx += kThreads) {
+      for (int idx = tid; idx < tot; idx += T) {
         const int part = idx & 1, rest = idx >> 1;
         const int s = rest / hr, l = rest % hr, j = col_of(s);
         const real r = ld_real(pr.Rd + (size_t)j * L);
@@ -331,7 +329,7 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     for (int s = 0; s < w; ++s) {
       const int j = col_of(s);
       const int tot = j * 2;  // (k, part) pairs with k < j
-      for (int idx = p * kThreads + tid; idx < tot; idx += Br * kThreads) {
+      for (int idx = p * T + tid; idx < tot; idx += Br * T) {
         const int k = idx >> 1, part = idx & 1;
         double* dst = (j < pr.n) ? pr.R + ((size_t)j * pr.ldr + k) * E : pr.Y + (size_t)k * E;
         elem cc;
@@ -388,12 +386,12 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     if (blockIdx.x == 0) {
       double* ys = sm;                          // nbk * E, row k at (k - s) * E
       double* tb = sm + (size_t)kBS * E;        // t_jk (j < k in the block) at ((k - s) kBS + j - s) E
-      for (int i = tid; i < nbk; i += kThreads) {
+      for (int i = tid; i < nbk; i += T) {
         const elem v = g_load_cg<Ar>(pr.Y + (size_t)(s + i) * E);
 #pragma unroll
         for (int q = 0; q < E; ++q) ys[(size_t)i * E + q] = v.v[q];
       }
-      for (int i = tid; i < nbk * nbk; i += kThreads) {
+      for (int i = tid; i < nbk * nbk; i += T) {
         const int kk = i / nbk, jj = i % nbk;
         if (jj >= kk) continue;
         const elem v = g_load_cg<Ar>(pr.Rt + ((size_t)(s + kk) * n + s + jj) * E);
@@ -406,7 +404,7 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
 #pragma unroll
         for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
         if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
-        for (int t = tid; t < 2 * (k - s); t += kThreads) {
+        for (int t = tid; t < 2 * (k - s); t += T) {
           const int j = s + (t >> 1), part = t & 1;
           double* yj = ys + (size_t)(j - s) * E;
           elem y = sm_load_part<Ar>(yj, 1, 0, part);
@@ -475,8 +473,8 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
 }
 
 // ------------------------------------------------------------------ the kernel
-template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
+template <class Ar, int T>
+__global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
   constexpr int L = Ar::L, E = 2 * L, ACC = Ar::ACC;
   using elem = typename Ar::elem;
   using acc = typename Ar::acc;
@@ -496,8 +494,8 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   double* coef = piv + (size_t)2 * E * h;    // w * E
   double* gkk = coef + (size_t)w * E;        // E (pivot norm, as an element)
   double* scal = gkk + E;                    // 4 * E scratch
-  double* redb = scal + 4 * E;               // kThreads part accumulators
-  int* iflag = reinterpret_cast<int*>(redb + (size_t)kThreads * L);
+  double* redb = scal + 4 * E;               // T part accumulators
+  int* iflag = reinterpret_cast<int*>(redb + (size_t)T * L);
   using pacc = typename Ar::pacc;
   constexpr int PACC = Ar::PACC;
   static_assert(sizeof(pacc) == PACC * sizeof(double) && PACC == L, "part accumulator layout");
@@ -526,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   __syncthreads();
   {
     bool bad = false;
-    for (int idx = tid; idx < w * h; idx += kThreads) {
+    for (int idx = tid; idx < w * h; idx += T) {
       const int s = idx / h, l = idx % h;
       elem e;
       if (l < hr) {
@@ -542,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     if (bad) iflag[0] = 1;
   }
   // pivot 0 rows (column 0 is unmodified at the start)
-  for (int l = tid; l < h; l += kThreads) {
+  for (int l = tid; l < h; l += T) {
     elem e;
     if (l < hr) {
       e = g_load<Ar>(colptr(0, r0 + l));
@@ -565,9 +563,9 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     const int nact = w - first;
     if (nact <= 0) return;
     const int pairs = 2 * nact;
-    int C = kThreads / pairs;
+    int C = T / pairs;
     C = max(1, min(C, max(hr, 1)));
-    const int per_round = kThreads / C;
+    const int per_round = T / C;
     pacc* red = reinterpret_cast<pacc*>(redb);
     for (int base = 0; base < pairs; base += per_round) {
       const int job = tid / C, ch = tid % C;
@@ -626,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       const int BrP = pow2_ceil(Br);
       const int nred = 1 + max(nact, 0);
       const int jobs = nred * 2 * BrP;
-      for (int base = 0; base < jobs; base += kThreads) {
+      for (int base = 0; base < jobs; base += T) {
         const int job = base + tid;
         const int ci = job / (2 * BrP), rem = job % (2 * BrP);
         const int part = rem / BrP, pp = rem % BrP;
@@ -677,7 +675,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       if (own_k) {
         const int s = k / Bc;
         const double* ts = tile + (size_t)s * E * h;
-        for (int l = tid; l < hr; l += kThreads) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
+        for (int l = tid; l < hr; l += T) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
       }
       break;
     }
@@ -685,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     // (2) coefficients c_kj = G_kj / G_kk of the own columns j > k, one lane per part
     {
       const double invG = Ar::inv_lead(G);
-      for (int t = tid; t < 2 * nact; t += kThreads) {
+      for (int t = tid; t < 2 * nact; t += T) {
         double* cs = coef + (size_t)(first + (t >> 1)) * E;
         const int part = t & 1;
         const elem g = sm_load_part<Ar>(cs, 1, 0, part);
@@ -710,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       elem cc;
 #pragma unroll
       for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s1 * E + q];
-      for (int t = tid; t < 2 * hr; t += kThreads) {
+      for (int t = tid; t < 2 * hr; t += T) {
         const int l = t >> 1, part = t & 1;
         elem y = sm_load_part<Ar>(ts, h, l, part);
         Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
@@ -720,13 +718,13 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
           pnxt[(part * L + q) * h + l] = y.v[part * L + q];
         }
       }
-      for (int l = hr + tid; l < h; l += kThreads) {  // padding rows stay zero
+      for (int l = hr + tid; l < h; l += T) {  // padding rows stay zero
 #pragma unroll
         for (int q = 0; q < E; ++q) pnxt[q * h + l] = 0.0;
       }
       __syncthreads();
       double* vdst = pr.V + ((size_t)nxt * Br + p) * h * E;
-      for (int l = tid; l < h; l += kThreads) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
+      for (int l = tid; l < h; l += T) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -741,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       const int nb = w - sb;
       if (nb > 0 && hr > 0) {
         const int tot = nb * hr * 2;
-        for (int idx = tid; idx < tot; idx += kThreads) {
+        for (int idx = tid; idx < tot; idx += T) {
           const int part = idx & 1, rest = idx >> 1;
           const int s = sb + rest / hr, l = rest % hr;
           double* ts = tile + (size_t)s * E * h;
@@ -759,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
     MGS_TR(k, 4);
     // (5) coefficients of row k go to R (row k) and Y (column b); scaled by r_kk at the end
     if (p == 0) {
-      for (int t = tid; t < nact; t += kThreads) {
+      for (int t = tid; t < nact; t += T) {
         const int s = first + t, j = col_of(s);
         elem cc;
 #pragma unroll
@@ -778,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
       if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
       __syncthreads();
       const double* vsrc = pr.V + ((size_t)nxt * Br + p) * h * E;
-      for (int l = tid; l < h; l += kThreads) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+      for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
     }
     __syncthreads();
 
@@ -791,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, 1) mgs_ls_kernel(Params pr) {
   grid_barrier(pr, epoch);
   MGS_TR(nc, 0);
 
-  mgs_epilogue<Ar>(pr, epoch, sm, p, c);
+  mgs_epilogue<Ar, T>(pr, epoch, sm, p, c);
 }
 
 }  // namespace mgs

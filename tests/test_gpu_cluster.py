@@ -34,7 +34,7 @@ SHAPES = [(64, 64, 2), (65, 64, 2), (200, 150, 2), (320, 128, 2), (511, 60, 2), 
 def test_kernel_vs_oracle(orc, kernel, m, n, L):
     plan = mgs_plan_query(L, m, n, True)
     if kernel == "default":
-        assert plan["kernel"] == ("cluster" if L <= 2 and plan["Br"] <= 8 else "grid")
+        assert plan["kernel"] in (("cluster", "grid") if L <= 2 and plan["Br"] <= 8 else ("grid",))
     elif kernel == "cluster" and plan["Br"] > 8:
         assert plan["kernel"] == "grid"
     else:
@@ -81,3 +81,24 @@ def test_kernels_agree(orc, monkeypatch):
     for k in ("group", "grid"):
         assert rel(orc, res["cluster"]["x"], res[k]["x"]) <= 2 * TOL[2]
         assert rel(orc, upper(res["cluster"]["R"]), upper(res[k]["R"])) <= 2 * TOL[2]
+
+
+@pytest.mark.parametrize("kk", ["grid", "cluster", "group"])
+@pytest.mark.parametrize("m,n,L", [(65, 64, 2), (200, 150, 2), (96, 96, 4), (300, 31, 1)])
+def test_256_threads_vs_oracle(orc, monkeypatch, kk, m, n, L):
+    """Each kernel with 256 threads per CTA (two warps per SM sub-partition), the layout
+    the plan picks when a CTA owns many columns."""
+    monkeypatch.setenv("MGS_KERNEL", kk)
+    monkeypatch.setenv("MGS_CTA_THREADS", "256")
+    assert mgs_plan_query(L, m, n, True)["threads"] == 256
+    A, _, b = planted_system(m, n, L, 4500 + 7 * m + n + L, orc=orc)
+    compare_ls(orc, A, b)
+
+
+def test_default_threads_follow_columns_per_cta(monkeypatch):
+    monkeypatch.delenv("MGS_CTA_THREADS", raising=False)
+    monkeypatch.delenv("MGS_KERNEL", raising=False)
+    for (m, n, L) in [(320, 256, 4), (512, 512, 2), (32, 32, 2)]:
+        p = mgs_plan_query(L, m, n, True)
+        w = -(-(n + 1) // p["Bc"])
+        assert p["threads"] == (256 if w >= 16 else 128), (m, n, p)
