@@ -64,3 +64,27 @@ def test_host_argument_checks(lib):
     # QR needs R
     assert L.mgs_qr_dd(good, 4, None, 4, 4, 4, good, 1 << 20, st, None) == 1
     assert L.mgs_status_string(2) == b"MGS_ERANK"
+
+
+def test_host_argument_checks_newton_and_batched(lib):
+    """The Newton step and the batched solve reject bad arguments (including empty
+    problems) on the host, before any CUDA call."""
+    from paper_1210_0800_gb300 import _binding
+
+    L = _binding.load()
+    vp, c_double = ctypes.c_void_p, ctypes.c_double
+    good = vp(4096)
+    st = vp(8192)
+    args = lambda J, ldj, x, m, n, tol: (J, ldj, good, x, m, n, c_double(tol), good, good, 1 << 20, st, None)
+    assert L.newton_step_dd(*args(None, 4, good, 4, 4, 0.0)) == 1      # null J
+    assert L.newton_step_dd(*args(good, 4, good, 3, 4, 0.0)) == 1      # m < n
+    assert L.newton_step_qd(*args(good, 4, good, 4, 0, 0.0)) == 1      # n = 0 (empty)
+    assert L.newton_step_d(*args(good, 2, good, 4, 4, 0.0)) == 1       # ldj < m
+    assert L.newton_step_dd(*args(good, 4, good, 4, 4, -1.0)) == 1     # negative tolerance
+    assert L.newton_step_dd(*args(good, 4, vp(4104), 4, 4, 0.0)) == 1  # misaligned x
+    i64 = vp(4096)
+    bargs = lambda batch, max_m, max_n, A: (A, good, good, None, i64, i64, i64, None, good, good, None, batch,
+                                            max_m, max_n, good, 1 << 20, st, None, None)
+    assert L.ls_solve_dd_batched(*bargs(0, 4, 4, good)) == 1           # empty batch
+    assert L.ls_solve_qd_batched(*bargs(8, 3, 4, good)) == 1           # max_m < max_n
+    assert L.ls_solve_d_batched(*bargs(8, 4, 4, vp(4104))) == 1        # misaligned pool
