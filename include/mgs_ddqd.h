@@ -157,6 +157,11 @@ int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, do
 typedef struct {
   int threads;     /* threads per CTA: 128 or 256 (0 = 256) */
   int ctas_per_sm; /* resident CTAs per SM, 1..4 (0 = 1) */
+  int split;       /* CTAs per system, 1, 2 or 4 (0 = automatic: 2 or 4 when the batch is
+                      smaller than half or a quarter of the resident CTAs and every slice
+                      keeps 32 rows); the CTAs of a system form a thread-block cluster, each
+                      holds a slice of the rows, the slices' Gram partials are summed
+                      through distributed shared memory */
 } mgs_tune;
 
 size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, const mgs_tune* tune);

@@ -25,7 +25,7 @@ EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_works
 
 class MgsTune(ctypes.Structure):
     """Launch shape of the batched solve (mgs_tune in the C header)."""
-    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("split", ctypes.c_int)]
 
 _lib = None
 

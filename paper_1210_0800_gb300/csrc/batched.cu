@@ -13,7 +13,7 @@ void set_last_cuda_error(int code);
 namespace {
 
 struct BPlan {
-  int T, per_sm, grid;
+  int T, per_sm, grid, S;  // S: CTAs per system (a thread-block cluster when > 1)
   size_t smem, off_scr, total;
   long long per_cta;
 };
@@ -27,25 +27,58 @@ bool make_bplan(int L, int batch, int max_m, int max_n, const mgs_tune* tune, BP
   bp.per_sm = (tune && tune->ctas_per_sm) ? tune->ctas_per_sm : 1;
   if (bp.T != 128 && bp.T != 256) return false;
   if (bp.per_sm < 1 || bp.per_sm > 4) return false;
-  bp.smem = mgs::batched_smem_bytes(L, bp.T, max_m, max_n);
+  // systems split over S CTAs when the batch is smaller than the GPU (each slice keeps at
+  // least 32 rows); automatic unless the tuning asks for a split
+  if (tune && tune->split) {
+    bp.S = tune->split;
+    if (bp.S != 1 && bp.S != 2 && bp.S != 4) return false;
+  } else {
+    bp.S = 1;
+    while (bp.S < 4 && (long long)batch * 2 * bp.S <= (long long)sms * bp.per_sm && max_m / (2 * bp.S) >= 32)
+      bp.S *= 2;
+  }
+  bp.smem = mgs::batched_smem_bytes(L, bp.T, max_m, max_n, bp.S);
   if (bp.smem > 227 * 1024) return false;
-  bp.grid = sms * bp.per_sm;
-  if (bp.grid > batch) bp.grid = batch;
+  const int clusters = (sms * bp.per_sm) / bp.S;
+  bp.grid = bp.S * (clusters < batch ? clusters : batch);
   bp.per_cta = mgs::batched_scratch_doubles(L, max_n);
   bp.off_scr = 256;
   bp.total = bp.off_scr + sizeof(double) * (size_t)bp.per_cta * bp.grid;
   return true;
 }
 
-template <class Ar, int T>
-int launch_batched(const mgs::BatchParams& p, const BPlan& pl, cudaStream_t st) {
-  auto kern = mgs::mgs_batched_kernel<Ar, T>;
+template <class Ar, int T, int S>
+int launch_batched_s(const mgs::BatchParams& p, const BPlan& pl, cudaStream_t st) {
+  auto kern = mgs::mgs_batched_kernel<Ar, T, S>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return (int)e;
   mgs::BatchParams copy = p;
   void* args[] = {&copy};
-  e = cudaLaunchKernel((const void*)kern, dim3(pl.grid), dim3(T), args, pl.smem, st);
-  return (int)e;
+  if constexpr (S == 1) {
+    return (int)cudaLaunchKernel((const void*)kern, dim3(pl.grid), dim3(T), args, pl.smem, st);
+  } else {
+    // the clusters work independently (no CTA waits for another cluster)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.grid);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = pl.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = S;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+  }
+}
+
+template <class Ar, int T>
+int launch_batched(const mgs::BatchParams& p, const BPlan& pl, cudaStream_t st) {
+  return pl.S == 4 ? launch_batched_s<Ar, T, 4>(p, pl, st)
+         : pl.S == 2 ? launch_batched_s<Ar, T, 2>(p, pl, st)
+                     : launch_batched_s<Ar, T, 1>(p, pl, st);
 }
 
 int run_batched(int L, double* A, double* b, double* x, double* R, const int64_t* a_off, const int64_t* b_off,

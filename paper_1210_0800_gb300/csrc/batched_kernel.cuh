@@ -10,7 +10,15 @@
 // against the pivot (one lane per (column, part, row chunk)), a shared-memory tree,
 // c_kj = G_kj / G_kk, the update a_j -= c_kj a_k.  Normalisation and the scaled back
 // substitution follow the single-system kernel.
+//
+// Split systems (S = 2 or 4, for batches smaller than the GPU): the S CTAs of a
+// thread-block cluster share one system, each keeping a contiguous slice of its rows; the
+// Gram partials of the slices are summed through distributed shared memory in rank order,
+// so every CTA derives the same coefficients; the normalisation is split by rows and the
+// back substitution runs on rank 0.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include <cstdint>
 
@@ -39,13 +47,14 @@ struct BatchParams {
   double one, nzero;
 };
 
-// Shared memory of one batched CTA.
-__host__ __device__ inline size_t batched_smem_bytes(int L, int T, int max_m, int max_n) {
+// Shared memory of one batched CTA (S CTAs per system).
+__host__ __device__ inline size_t batched_smem_bytes(int L, int T, int max_m, int max_n, int S = 1) {
   const size_t E = 2 * (size_t)L;
   return sizeof(double) * ((size_t)max_m * E          // pivot column
                            + (size_t)(max_n + 1) * E  // coefficients / Gram row
                            + (size_t)T * L            // reduction tree
-                           + 2 * E)
+                           + 2 * E                    //
+                           + (S > 1 ? 2 * (size_t)(max_n + 1) * 2 * L : 0))  // slice partials, 2 buffers
          + 16 * sizeof(int);
 }
 
@@ -57,23 +66,35 @@ __host__ __device__ inline long long batched_scratch_doubles(int L, int max_n) {
   return (v + 31) / 32 * 32;
 }
 
-template <class Ar, int T>
+template <class Ar, int T, int S>
 __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
+  namespace cg = cooperative_groups;
   constexpr int L = Ar::L, E = 2 * L;
   using elem = typename Ar::elem;
   using real = typename Ar::real;
   using pacc = typename Ar::pacc;
   constexpr int PACC = Ar::PACC;
+  static_assert(S == 1 || S == 2 || S == 4, "CTAs per system");
   const Fp f{bp.one, bp.nzero};
   const int tid = threadIdx.x;
+  const int rank = (int)(blockIdx.x % S);  // the cluster is S consecutive CTAs
+  const bool lead = rank == 0;
 
   extern __shared__ __align__(16) double sm[];
-  double* piv = sm;                               // max_m * E, element l at l * E
+  double* piv = sm;                               // max_m * E, slice row l at l * E
   double* gbuf = piv + (size_t)bp.max_m * E;       // (max_n + 1) * E
   pacc* red = reinterpret_cast<pacc*>(gbuf + (size_t)(bp.max_n + 1) * E);  // T
-  int* sflag = reinterpret_cast<int*>(reinterpret_cast<double*>(red) + (size_t)T * L + 2 * E);
+  double* pslice = reinterpret_cast<double*>(red) + (size_t)T * L + 2 * E;  // S > 1: 2 x (max_n + 1) x 2 x PACC
+  int* sflag = reinterpret_cast<int*>(pslice + (S > 1 ? 2 * (size_t)(bp.max_n + 1) * 2 * PACC : 0));
+  // cluster barrier (S > 1): orders shared- and global-memory accesses of the S CTAs
+  auto csync = [&]() {
+    if constexpr (S > 1)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
+  };
 
-  double* scr = bp.ws + (size_t)blockIdx.x * bp.per_cta;
+  double* scr = bp.ws + (size_t)(blockIdx.x / S) * bp.per_cta;  // shared by the cluster
   double* Rp = scr;  // packed upper triangle: (k, j), k <= j, at (j (j + 1) / 2 + k) * E
   double* Yv = Rp + (size_t)bp.max_n * (bp.max_n + 1) / 2 * E;
   double* Gd = Yv + (size_t)(bp.max_n + 1) * E;
@@ -107,13 +128,19 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
   auto packed = [](int k, int j) { return (size_t)j * (j + 1) / 2 + k; };
 
   for (;;) {
-    __syncthreads();
+    csync();  // the cluster is done with the previous system
     if (tid == 0) {
-      sflag[0] = (int)atomicAdd(bp.counter, 1u);
+      if (lead) sflag[0] = (int)atomicAdd(bp.counter, 1u);
       sflag[1] = ST_OK;
     }
-    __syncthreads();
-    const int qi = sflag[0];
+    csync();
+    int qi;
+    if constexpr (S > 1) {
+      qi = *cg::this_cluster().map_shared_rank(sflag, 0);
+      csync();  // no CTA leaves while a peer still reads rank 0's shared memory
+    } else {
+      qi = sflag[0];
+    }
     if (qi >= bp.batch) break;
     const int sys = bp.order ? bp.order[qi] : qi;
     const int m = bp.m_arr[sys], n = bp.n_arr[sys];
@@ -126,25 +153,29 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
     double* bv = bp.b + (size_t)bp.b_off[sys] * E;
     double* xv = bp.x + (size_t)bp.x_off[sys] * E;
     auto col = [&](int j) -> double* { return (j < n) ? A + (size_t)j * m * E : bv; };
-    // non-finite input check
+    // this CTA's slice of the rows
+    const int mr = (m + S - 1) / S;
+    const int r0 = min(m, rank * mr), ml = min(m, r0 + mr) - r0;
+    // non-finite input check (own slice)
     {
       bool bad = false;
-      for (int i = tid; i < m * nc * E; i += T) {
-        const int j = i / (m * E), r = i % (m * E);
-        bad |= !finite64(col(j)[r]);
+      for (int i = tid; i < ml * nc * E; i += T) {
+        const int j = i / (ml * E), r = i % (ml * E);
+        bad |= !finite64(col(j)[(size_t)r0 * E + r]);
       }
       if (bad) sflag[1] = ST_ENONFINITE;
     }
     __syncthreads();
 
     for (int k = 0; k < nc; ++k) {
-      // pivot column rows
-      for (int i = tid; i < m * E; i += T) piv[i] = col(k)[i];
+      // pivot column rows of the slice
+      for (int i = tid; i < ml * E; i += T) piv[i] = col(k)[(size_t)r0 * E + i];
       __syncthreads();
       // Gram row G_kj, j >= k: (column, part, row chunk) items; tree over chunks
       const int cols = nc - k, pairs = 2 * cols;
+      double* pout = pslice + (size_t)(k & 1) * (bp.max_n + 1) * 2 * PACC;
       int C = T / pairs;
-      C = max(1, min(C, m));
+      C = max(1, min(C, max(ml, 1)));
       const int per_round = T / C;
       for (int base = 0; base < pairs; base += per_round) {
         const int job = tid / C, ch = tid % C, pi = base + job;
@@ -153,8 +184,8 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
         pacc a;
         Ar::pzero(a);
         if (act && !(j == k && part == 1)) {
-          const double* cj = col(j);
-          for (int l = ch; l < m; l += C) {
+          const double* cj = col(j) + (size_t)r0 * E;
+          for (int l = ch; l < ml; l += C) {
             elem pe, ce;
 #pragma unroll
             for (int q = 0; q < E; ++q) {
@@ -175,19 +206,51 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
           __syncthreads();
         }
         if (act && ch == 0) {
+          if constexpr (S > 1) {
+            const double* src = reinterpret_cast<const double*>(&red[tid]);
+#pragma unroll
+            for (int q = 0; q < PACC; ++q) pout[(size_t)pi * PACC + q] = src[q];
+          } else {
+            double* dst = gbuf + (size_t)(j - k) * E + part * L;
+            if (j == k && part == 1) {
+#pragma unroll
+              for (int q = 0; q < L; ++q) dst[q] = 0.0;
+            } else {
+              Ar::pfinal(f, red[tid], dst);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if constexpr (S > 1) {
+        // sum the S slices' partials in rank order (the same order in every CTA)
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        for (int t = tid; t < pairs; t += T) {
+          const int j = k + (t >> 1), part = t & 1;
           double* dst = gbuf + (size_t)(j - k) * E + part * L;
           if (j == k && part == 1) {
 #pragma unroll
             for (int q = 0; q < L; ++q) dst[q] = 0.0;
-          } else {
-            Ar::pfinal(f, red[tid], dst);
+            continue;
           }
+          pacc a;
+          Ar::pzero(a);
+          for (int pr = 0; pr < S; ++pr) {
+            const double* src = cl.map_shared_rank(pout, pr) + (size_t)t * PACC;
+            pacc o;
+            double* od = reinterpret_cast<double*>(&o);
+#pragma unroll
+            for (int q = 0; q < PACC; ++q) od[q] = src[q];
+            Ar::pcombine(f, a, o);
+          }
+          Ar::pfinal(f, a, dst);
         }
         __syncthreads();
       }
       const real G = ld_real(gbuf);
       const bool okpiv = Ar::positive(G);
-      if (tid == 0) st_real(Gd + (size_t)k * L, G);
+      if (lead && tid == 0) st_real(Gd + (size_t)k * L, G);
       if (k == nc - 1) break;  // the right-hand side: keep G (z^2); its column is the residual
       if (!okpiv && tid == 0) sflag[1] = (sflag[1] == ST_OK) ? ST_ERANK : sflag[1];
       // coefficients c_kj = G_kj / G_kk (j > k), stored as row k of R (or y_k)
@@ -204,15 +267,15 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
           for (int q = 0; q < E; ++q) cc.v[q] = 0.0;
         }
         st_part(g, cc, part);
-        st_part((j < n) ? Rp + packed(k, j) * E : Yv + (size_t)k * E, cc, part);
+        if (lead) st_part((j < n) ? Rp + packed(k, j) * E : Yv + (size_t)k * E, cc, part);
       }
       __syncthreads();
-      // update a_j -= c_kj a_k, j > k (one lane per (column, row, part))
-      const int tot = (cols - 1) * m * 2;
+      // update a_j -= c_kj a_k, j > k (one lane per (column, slice row, part))
+      const int tot = (cols - 1) * ml * 2;
       for (int idx = tid; idx < tot; idx += T) {
         const int part = idx & 1, rest = idx >> 1;
-        const int j = k + 1 + rest / m, l = rest % m;
-        double* p = col(j) + (size_t)l * E;
+        const int j = k + 1 + rest / ml, l = rest % ml;
+        double* p = col(j) + (size_t)(r0 + l) * E;
         elem y = ld_part(p, part), cc, pe;
 #pragma unroll
         for (int q = 0; q < E; ++q) {
@@ -225,25 +288,29 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
       __syncthreads();
     }
     __syncthreads();
-    // r_kk, 1/r_kk
-    for (int k = tid; k < nc; k += T) {
-      const real r = Ar::sqrt(f, ld_real(Gd + (size_t)k * L));
-      st_real(Rd + (size_t)k * L, r);
-      if (Ar::positive(r)) st_real(Ri + (size_t)k * L, Ar::inv_real(f, r));
-    }
-    __syncthreads();
-    // q_j = a_j / r_jj; the last column (b) is the residual and stays
-    for (int idx = tid; idx < n * m * 2; idx += T) {
+    // r_kk, 1/r_kk (rank 0, into the cluster's scratch)
+    if (lead)
+      for (int k = tid; k < nc; k += T) {
+        const real r = Ar::sqrt(f, ld_real(Gd + (size_t)k * L));
+        st_real(Rd + (size_t)k * L, r);
+        if (Ar::positive(r)) st_real(Ri + (size_t)k * L, Ar::inv_real(f, r));
+      }
+    __threadfence();
+    csync();
+    // q_j = a_j / r_jj over the slice; the last column (b) is the residual and stays
+    for (int idx = tid; idx < n * ml * 2; idx += T) {
       const int part = idx & 1, rest = idx >> 1;
-      const int j = rest / m, l = rest % m;
+      const int j = rest / ml, l = rest % ml;
       const real r = ld_real(Rd + (size_t)j * L);
       if (!Ar::positive(r)) continue;
-      double* p = col(j) + (size_t)l * E;
+      double* p = col(j) + (size_t)(r0 + l) * E;
       const elem a = ld_part(p, part);
       elem q = a;
       Ar::div_real_part(f, q, a, r, Ar::inv_lead(r), part);
       st_part(p, q, part);
     }
+    // the rest is rank 0's: R, back substitution, x, status
+    if (!lead) continue;
     // optional R output (packed upper triangle): r_kj = c_kj r_kk, real diagonal r_jj
     if (bp.R) {
       double* Ro = bp.R + (size_t)bp.r_off[sys] * E;
@@ -316,7 +383,15 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
       st_part(xv + (size_t)k * E, xo, part);
     }
     __syncthreads();
-    if (tid == 0) bp.status[sys] = sflag[1];
+    if (tid == 0) {
+      // the input check comes first: a non-finite entry in any slice wins over the
+      // rank deficiency it causes (the other flags are the same in every slice)
+      int stv = sflag[1];
+      if constexpr (S > 1)
+        for (int pr = 1; pr < S; ++pr)
+          if (*cg::this_cluster().map_shared_rank(sflag + 1, pr) == ST_ENONFINITE) stv = ST_ENONFINITE;
+      bp.status[sys] = stv;
+    }
   }
 }
 

@@ -100,3 +100,47 @@ def test_autotuner_picks_a_candidate(tmp_path):
     assert tuple(best) in tune.CANDIDATES and len(times) == len(tune.CANDIDATES)
     again, _ = tune.tune_batched(bt, cache_path=str(tmp_path / "c.json"))
     assert tuple(again) == tuple(best)
+
+
+@pytest.mark.parametrize("L,split", [(2, 2), (2, 4), (4, 2), (1, 4)])
+def test_split_systems_vs_oracle(orc, L, split):
+    """Systems shared by a cluster of 2 or 4 CTAs (row slices, partials summed through
+    distributed shared memory) agree with the oracle; tiny systems leave slices empty."""
+    systems = ragged(orc, L, 12, 64 + split + L, n_lo=1, n_hi=60, extra_hi=12)
+    bt, st = run(systems, tune=(256, 1, split))
+    assert (st == 0).all(), st
+    for i, (A, b) in enumerate(systems):
+        Q, r, x = unpack(bt, i, systems)
+        o = orc.ls_solve(A.copy(), b.copy())
+        assert rel(orc, x, o["x"]) <= TOL[L], i
+        assert rel(orc, Q, o["Q"]) <= TOL[L], i
+        d, _ = orc.max_abs_diff(r, o["resid"])
+        assert d <= TOL[L] * max(1.0, orc.max_abs_diff(b, 0 * b)[0]), i
+
+
+def test_split_statuses(orc):
+    """Per-system statuses with split systems: a rank-deficient and a non-finite system
+    among clean ones, the non-finite entry in a slice other than rank 0's."""
+    systems = ragged(orc, 2, 6, 65, n_lo=8, n_hi=20, extra_hi=40)
+    A, b = systems[1]
+    A[2] = 0.0
+    A, b = systems[3]
+    A[1, A.shape[1] - 1, 0, 0] = np.inf
+    bt, st = run(systems, tune=(128, 1, 4))
+    assert st[1] == 2 and st[3] == 3
+    assert (np.delete(st, [1, 3]) == 0).all(), st
+
+
+def test_automatic_split_for_small_batches(orc):
+    """A batch much smaller than the GPU is split automatically and still agrees."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    systems = ragged(orc, 2, 16, 66, n_lo=60, n_hi=90, extra_hi=16)
+    bt, st = run(systems)
+    assert (st == 0).all()
+    for i in (0, 7, 15):
+        A, b = systems[i]
+        Q, r, x = unpack(bt, i, systems)
+        assert rel(orc, x, orc.ls_solve(A.copy(), b.copy())["x"]) <= TOL[2]
