@@ -53,6 +53,61 @@ DEFAULT = "c1_qd_320x256"
 SWEEP = ["dd_64", "dd_128", "dd_256", "dd_512", "qd_64", "qd_128", "qd_256", "qd_512"]
 
 
+# The paper's wall-clock seconds for 10,000 runs of MGS + one back substitution on m = n
+# systems (Tesla C2050 and one core of a Xeon X5690): Table 4 (complex double) and
+# Table 5 (complex double double, complex quad double).  Quoted as context only.
+PAPER_TABLES = {
+    1: {16: (2.01, 4.11), 32: (14.61, 6.52), 48: (47.80, 11.11), 64: (112.60, 15.38), 80: (217.52, 22.89),
+        96: (373.06, 30.43), 112: (589.35, 40.82), 128: (876.11, 49.10), 144: (1243.26, 67.41),
+        160: (1701.57, 80.42), 176: (2260.07, 99.94), 192: (2932.15, 116.90), 208: (3722.77, 149.45),
+        224: (4641.71, 172.30), 240: (5703.77, 211.30), 256: (6935.10, 234.29)},
+    2: {16: (17.17, 11.85), 32: (125.06, 22.44), 48: (408.20, 35.88), 64: (952.35, 55.18), 80: (1841.07, 79.11)},
+    4: {16: (113.51, 143.07), 32: (813.65, 155.32), 48: (2556.36, 266.55), 64: (6216.06, 409.57),
+        80: (12000.15, 597.47)},
+}
+
+
+def run_tables(args):
+    """The sizes of the paper's Tables 4 and 5: per (limbs, n) the time of 10,000 solves
+    on this GPU (distinct systems, inputs cold), one JSON line each, beside the paper's
+    CPU and C2050 seconds."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    K, W = args.steps, args.warmup
+    for L in (1, 2, 4):
+        fn = {1: mg.ls_solve_d, 2: mg.ls_solve_dd, 4: mg.ls_solve_qd}[L]
+        for n, (cpu_s, gpu_s) in sorted(PAPER_TABLES[L].items()):
+            host = [inputs.system(n, n, L, inputs.system_seed(inputs.BASE_SEED + 5, i)) for i in range(K + W)]
+            As = [torch.from_numpy(h[0]).to(dev) for h in host]
+            bs = [torch.from_numpy(h[2]).to(dev) for h in host]
+            x = torch.empty((n, 2, L), dtype=torch.float64, device=dev)
+            ws = torch.empty(mg.mgs_workspace_bytes(L, n, n, True), dtype=torch.uint8, device=dev)
+            st = torch.zeros(K + W, dtype=torch.int32, device=dev)
+            for i in range(W):
+                fn(As[i], bs[i], x=x, workspace=ws, status=st[i:i + 1])
+            torch.cuda.synchronize(dev)
+            flush_l2(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(W, K + W):
+                fn(As[i], bs[i], x=x, workspace=ws, status=st[i:i + 1])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / K
+            ours_s = 10000 * ms / 1000.0
+            print(json.dumps({
+                "table": "Table 4" if L == 1 else "Table 5", "limbs": L, "m": n, "n": n,
+                "ms_per_solve": ms, "seconds_per_10000": ours_s, "paper_c2050_seconds": gpu_s,
+                "paper_cpu_seconds": cpu_s, "vs_c2050": gpu_s / ours_s,
+                "status_errors": int((st != 0).sum().item())}))
+    return 0
+
+
 def hbm_bytes(L: int, m: int, n: int) -> int:
     """Algorithmic HBM bytes of one solve: [A b] read, Q and the residual column written,
     x and the upper triangle of R written."""
@@ -628,7 +683,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="one line per point of the m = n in {64, 128, 256, 512} DD and QD sweep")
+    ap.add_argument("--tables", action="store_true",
+                    help="one line per size of the paper's Tables 4 and 5, beside its C2050 seconds")
     args = ap.parse_args(argv)
+    if args.tables and args.impl == "ours":
+        return run_tables(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1 and args.impl == "ours":
