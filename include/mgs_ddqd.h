@@ -5,8 +5,8 @@
  * Method: Verschelde & Yoffe, "Orthogonalization on a General Purpose Graphics Processing
  * Unit with Double Double and Quad Double Arithmetic".
  *
- * Number format.  A real number is L float64 limbs (L = 2: double-double, L = 4:
- * quad-double) whose exact sum is its value, largest limb first.  A complex element is
+ * Number format.  A real number is L float64 limbs (L = 1: double, L = 2: double-double,
+ * L = 4: quad-double) whose exact sum is its value, largest limb first.  A complex element is
  * 2L consecutive doubles {re_0..re_{L-1}, im_0..im_{L-1}} (32 bytes for DD, 64 for QD).
  * Matrices are column-major BY ELEMENT: element (i, j) of a matrix with leading
  * dimension ld starts at base + (j * ld + i) * 2L doubles.  Vectors are contiguous.
@@ -24,9 +24,12 @@
  * MGS_ETIMEOUT.  The first error recorded wins.  Outputs are unspecified when the
  * status is not MGS_OK.  No exception crosses the ABI.
  *
- * Concurrency.  One call occupies the whole GPU with a cooperative launch (one CTA per
- * SM at most); calls on the same stream run one after another.  A workspace must not be
- * shared by calls that may run at the same time.
+ * Concurrency.  A single-system call occupies the whole GPU with one persistent launch
+ * of at most one CTA per SM whose CTAs wait for one another (a cooperative launch, or a
+ * launch of thread-block clusters whose residency the library checks first); calls on
+ * the same stream run one after another.  A workspace must not be shared by calls that
+ * may run at the same time.  The first call for a given size and device queries the
+ * device (occupancy); make it before capturing calls into a CUDA graph.
  */
 #ifndef MGS_DDQD_H
 #define MGS_DDQD_H
