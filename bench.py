@@ -190,6 +190,24 @@ def measured_traffic(workload: str):
     return t.get("traffic_bytes_per_launch", {}).get(workload)
 
 
+def max_over_ranks(values, device, world):
+    """Element-wise maximum over the ranks of per-rank timings: the slowest replica sets
+    the job's time (barrier-bracketed timed regions on every rank)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_seed(workload: str, rank: int, index: int) -> int:
+    """Seed of system `index` on `rank`: replicas solve distinct systems."""
+    return inputs.system_seed(inputs.workload_seed(workload), rank * 100000 + index)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -309,7 +327,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     K, W = args.steps, args.warmup
     total = K + W
     # distinct systems for every step (rank-dependent seeds: replicas solve different systems)
-    seeds = [inputs.system_seed(inputs.workload_seed(args.workload), rank * 100000 + i) for i in range(total)]
+    seeds = [replica_seed(args.workload, rank, i) for i in range(total)]
     host = [inputs.system(m, n, L, s, extreme=extreme) for s in seeds]
     As = [torch.from_numpy(h[0]).to(dev) for h in host]
     bs = [torch.from_numpy(h[2]).to(dev) for h in host]
@@ -377,14 +395,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     h2d = As[0].numel() * 8 + bs[0].numel() * 8
     d2h = xs[0].numel() * 8
 
-    # max over ranks
-    ms = ms_total
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_total, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms_total, e2e_ms], dev, world)
     if rank != 0:
         return 0
 
@@ -516,6 +527,7 @@ def run_gpu_batched(args, rank, world):
     torch.cuda.synchronize(dev)
     seq_ms = s0.elapsed_time(s1)
     seq_ops = sum(fp64_ops(L, host[i][0].shape[1], host[i][0].shape[0]) for i in sel)
+    ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], dev, world)
     if rank != 0:
         return 0
     value = world * batch * K / (ms_total / 1000.0)
@@ -582,8 +594,7 @@ def run_gpu_diff(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     K, W = args.steps, args.warmup
-    seed = inputs.system_seed(inputs.BASE_SEED + 4, rank)
-    host = [inputs.system(m, n, L, inputs.system_seed(seed, i)) for i in range(B)]
+    host = [inputs.system(m, n, L, replica_seed(args.workload, rank, i)) for i in range(B)]
     A0 = torch.from_numpy(np.stack([h[0] for h in host])).to(dev)
     b0 = torch.from_numpy(np.stack([h[2] for h in host])).to(dev)
     As = [A0.clone().requires_grad_(True) for _ in range(K + W)]
@@ -600,6 +611,10 @@ def run_gpu_diff(args, rank, world):
     flush_l2(dev)
     clocks = ClockSampler(local)
     time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     t0e.record(stream)
@@ -642,6 +657,7 @@ def run_gpu_diff(args, rank, world):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / Ke
+    ms, e2e_ms, fwd_ms = max_over_ranks([ms, e2e_ms, fwd_ms], dev, world)
     if rank != 0:
         return 0
     ops = B * fp64_ops(L, m, n)
