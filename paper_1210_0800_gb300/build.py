@@ -20,8 +20,10 @@ HOST_LIBRARY = os.path.join(LIBDIR, "libddqd_host.so")
 SOURCES = ["api.cu", "mgs_d.cu", "mgs_dd.cu", "mgs_qd.cu", "noalloc.cu", "batched.cu", "newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--fmad=false"]
-# extra nvcc flags for experiments (e.g. -DMGS_THREADS=256); empty by default
+# extra nvcc flags for experiments; empty by default
 EXTRA = os.environ.get("MGS_EXTRA_NVCC_FLAGS", "").split()
+# the phase-trace variant (kernels record global-timer stamps; see trace.py)
+TRACE_LIBRARY = os.path.join(LIBDIR, "trace", "libmgs_ddqd.so")
 
 
 def nvcc() -> str:
@@ -31,26 +33,30 @@ def nvcc() -> str:
     return path
 
 
-def _stale(objs) -> bool:
-    if not os.path.exists(LIBRARY):
+def _stale(library) -> bool:
+    if not os.path.exists(library):
         return True
-    t = os.path.getmtime(LIBRARY)
+    t = os.path.getmtime(library)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "mgs_ddqd.h"))
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(LIBDIR, exist_ok=True)
-    objdir = os.path.join(LIBDIR, "_obj")
+def build(force: bool = False, verbose: bool = False, trace: bool = False) -> str:
+    """Compile the library (trace=True: the phase-trace variant, in lib/trace/)."""
+    library = TRACE_LIBRARY if trace else LIBRARY
+    libdir = os.path.dirname(library)
+    os.makedirs(libdir, exist_ok=True)
+    objdir = os.path.join(libdir, "_obj")
     os.makedirs(objdir, exist_ok=True)
     objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
-    if not force and not _stale(objs):
-        return LIBRARY
+    if not force and not _stale(library):
+        return library
     cc = nvcc()
+    extra = EXTRA + (["-DMGS_TRACE=1"] if trace else [])
     procs = []
     for src, obj in zip(SOURCES, objs):
-        cmd = [cc, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -60,11 +66,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
         if verbose and out:
             sys.stdout.write(out.decode(errors="replace"))
-    tmp = LIBRARY + ".tmp"
+    tmp = library + ".tmp"
     link = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     subprocess.check_call(link)
-    os.replace(tmp, LIBRARY)
-    return LIBRARY
+    os.replace(tmp, library)
+    return library
 
 
 def build_host(force: bool = False) -> str:

@@ -1,0 +1,102 @@
+"""Phase timeline of one single-system solve (a diagnostic).
+
+The kernels compiled with -DMGS_TRACE=1 record, per CTA, a global-timer stamp at each
+phase boundary of every elimination step, the SM they ran on, and stamps of the
+normalisation and back-substitution phases.  This module builds that variant of the
+library (lib/trace/), runs a few solves of one size and prints where the time goes.
+
+    python -m paper_1210_0800_gb300.trace LIMBS M N      (MGS_KERNEL, MGS_ROWS apply)
+
+Phases of the grid-barrier kernel, per step k: reduction of the Br partial Gram rows,
+coefficient division, look-ahead update of column k+1, update of the other columns,
+wait for and copy of pivot k+1, partials of step k+1, grid barrier.  Of the cluster
+schedule: phase A (column k+1 on its owner), partials and cluster reduction, coefficient
+division, R/y stores and updates, wait for pivot k+1.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import sys
+
+import numpy as np
+
+from . import _binding, build, inputs
+
+GRID_PHASES = ["reduce", "coef", "lookahead", "update", "wait+copy", "partials", "barrier"]
+CLUSTER_PHASES = ["A (column k+1)", "partials+reduce", "coef", "store+update", "wait pivot"]
+
+
+def _load_trace_library():
+    lib = _binding.load(build.build(trace=True))
+    lib.mgs_trace_layout.restype = ctypes.c_int
+    lib.mgs_trace_layout.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_size_t),
+                                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    _binding._lib = lib  # the binding's calls below go to the trace variant
+    return lib
+
+
+def record(L: int, m: int, n: int, reps: int = 3, seed: int = 555):
+    """Run `reps` solves of one size with the trace variant; returns (plan, stamps) with
+    stamps[step, cta, slot] in nanoseconds (step n + 1 holds the epilogue stamps)."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    lib = _load_trace_library()
+    off, steps, ctas = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    if lib.mgs_trace_layout(L, m, n, 1, ctypes.byref(off), ctypes.byref(steps), ctypes.byref(ctas)) != 0:
+        raise RuntimeError("no layout for limbs=%d m=%d n=%d" % (L, m, n))
+    plan = mg.mgs_plan_query(L, m, n, True)
+    dev = torch.device("cuda:0")
+    fn = {1: mg.ls_solve_d, 2: mg.ls_solve_dd, 4: mg.ls_solve_qd}[L]
+    ws = torch.zeros(mg.mgs_workspace_bytes(L, m, n, True), dtype=torch.uint8, device=dev)
+    nbytes = 8 * 8 * steps.value * ctas.value
+    for rep in range(reps):
+        A, _, b = inputs.system(m, n, L, seed + rep)
+        ws[off.value: off.value + nbytes].zero_()
+        fn(torch.from_numpy(A).to(dev), torch.from_numpy(b).to(dev), workspace=ws)
+        torch.cuda.synchronize()
+    raw = ws[off.value: off.value + nbytes].cpu().numpy().view(np.uint64)
+    return plan, raw.reshape(steps.value, ctas.value, 8).astype(np.int64)
+
+
+def summarize(plan, tr) -> str:
+    """Per-phase sums of the per-step means over the CTAs active in the step."""
+    nc = tr.shape[0] - 1
+    sid = tr[0, :, 7]
+    lines = ["plan %s" % plan,
+             "CTAs %d on %d distinct SMs" % (len(sid), len(np.unique(sid)))]
+    grid = plan["kernel"] == "grid"
+    names = GRID_PHASES if grid else CLUSTER_PHASES
+    tot = np.zeros(len(names))
+    for k in range(nc - 1):
+        row = tr[k]
+        act = row[:, 0] > 0
+        if not act.any():
+            continue
+        for i in range(len(names)):
+            if grid and i == len(names) - 1:
+                nxt = tr[k + 1, act, 0]
+                tot[i] += np.mean(nxt - row[act, 6])
+            else:
+                tot[i] += np.mean(row[act, i + 1] - row[act, i])
+    t0 = tr[0, :, 0][tr[0, :, 0] > 0].min()
+    ep = tr[nc]
+    lines.append("sweep %.1f us, solve %.1f us" % ((ep[:, 0].max() - t0) / 1e3, (ep[:, 3].max() - t0) / 1e3))
+    for nm, v in zip(names, tot):
+        lines.append("  %-16s %9.1f us" % (nm, v / 1e3))
+    lines.append("  square roots %.1f us, Q and R scaling %.1f us, back substitution %.1f us" % (
+        np.mean(ep[:, 1] - ep[:, 0]) / 1e3, np.mean(ep[:, 2] - ep[:, 1]) / 1e3, np.mean(ep[:, 3] - ep[:, 2]) / 1e3))
+    return "\n".join(lines)
+
+
+def main(argv=None) -> int:
+    argv = sys.argv[1:] if argv is None else argv
+    L, m, n = (int(a) for a in argv[:3])
+    print(summarize(*record(L, m, n)))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
