@@ -164,6 +164,11 @@ struct D {
     y.v[0] = im ? y.v[0] : t;
     y.v[1] = im ? t : y.v[1];
   }
+  // y := y - c x, both parts (the operations of update_part, in the same order)
+  __host__ __device__ static __forceinline__ void update(const Fp& f, elem& y, const elem& c, const elem& x) {
+    y.v[0] = f.fma(c.v[1], x.v[1], f.fma(-c.v[0], x.v[0], y.v[0]));
+    y.v[1] = f.fma(-c.v[1], x.v[0], f.fma(-c.v[0], x.v[1], y.v[1]));
+  }
   __host__ __device__ static __forceinline__ double inv_lead(const real& r) { return rcp_rn(r.h); }
   __host__ __device__ static __forceinline__ void div_real_part(const Fp&, elem& q, const elem& a, const real& r,
                                                                double, int part) {

@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     if (nitB > 0) {
       auto slotB = [&](int it) { return norm_here ? (it == 0 ? -1 : sb + it - 1) : sb + it; };
       item_partials(pcur, nitB, slotB, pb);
+      MGS_TR(k, 6);
       group_sync();
       cluster_reduce(pb, nitB, [&](int it) { return norm_here && it == 0; });
     }
@@ -388,21 +389,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
       }
     }
     // update the columns of B
-    if (nb > 0 && hr > 0) {
-      const int tot = nb * hr * 2;
-      for (int idx = tid; idx < tot; idx += T) {
-        const int part = idx & 1, rest = idx >> 1;
-        const int s = sb + rest / hr, l = rest % hr;
-        double* ts = tile + (size_t)s * E * h;
-        elem cc;
-#pragma unroll
-        for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
-        elem y = sm_load_part<Ar>(ts, h, l, part);
-        Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
-#pragma unroll
-        for (int q = 0; q < L; ++q) ts[(part * L + q) * h + l] = y.v[part * L + q];
-      }
-    }
+    update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, nb);
     MGS_TR(k, 4);
     if (last) break;
     // the rows of pivot k+1

@@ -244,6 +244,47 @@ __device__ __forceinline__ typename Ar::acc acc_shfl_xor(const typename Ar::acc&
 __device__ __forceinline__ int pow2_floor(int v) { return v <= 1 ? 1 : 1 << (31 - __clz(v)); }
 __device__ __forceinline__ int pow2_ceil(int v) { return v <= 1 ? 1 : 1 << (32 - __clz(v - 1)); }
 
+// a_j -= c_j p for the tile slots [sb, sb + nb) over the CTA's hr rows (c_j at
+// coef + slot * 2L, the pivot rows in piv).  For D and DD with at least two elements per
+// thread a lane takes a whole element: its two parts are independent dependency chains the
+// FP64 pipe interleaves, and the element is loaded once (measured: +1-3 %; for QD the
+// doubled register state costs more than it gains).  Otherwise one lane per element part
+// keeps every lane busy.  Both mappings perform the same operations on every part.
+template <class Ar, int T>
+__device__ __forceinline__ void update_slots(const Fp& f, double* tile, const double* coef, const double* piv, int h,
+                                             int hr, int sb, int nb) {
+  constexpr int L = Ar::L, E = 2 * L;
+  using elem = typename Ar::elem;
+  const int tid = threadIdx.x;
+  if (nb <= 0 || hr <= 0) return;
+  const int elems = nb * hr;
+  if (L <= 2 && elems >= 2 * T) {
+    for (int idx = tid; idx < elems; idx += T) {
+      const int s = sb + idx / hr, l = idx % hr;
+      double* ts = tile + (size_t)s * E * h;
+      elem cc;
+#pragma unroll
+      for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
+      elem y = sm_load<Ar>(ts, h, l);
+      Ar::update(f, y, cc, sm_load<Ar>(piv, h, l));
+      sm_store<Ar>(ts, h, l, y);
+    }
+  } else {
+    for (int idx = tid; idx < 2 * elems; idx += T) {
+      const int part = idx & 1, rest = idx >> 1;
+      const int s = sb + rest / hr, l = rest % hr;
+      double* ts = tile + (size_t)s * E * h;
+      elem cc;
+#pragma unroll
+      for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
+      elem y = sm_load_part<Ar>(ts, h, l, part);
+      Ar::update_part(f, y, cc, sm_load<Ar>(piv, h, l), part);
+#pragma unroll
+      for (int q = 0; q < L; ++q) ts[(part * L + q) * h + l] = y.v[part * L + q];
+    }
+  }
+}
+
 // Shared-memory footprint (bytes) of one CTA.
 __host__ __device__ inline size_t smem_bytes(int L, int h, int w, int T) {
   const size_t E = 2 * (size_t)L;
@@ -733,25 +774,10 @@ __global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
     }
 
     MGS_TR(k, 3);
-    // (4) update the other own columns j > k+1 (one lane per element part)
+    // (4) update the other own columns j > k+1
     {
       const int sb = own_k1 ? first + 1 : first;  // slot of column k+1 is `first` when owned
-      const int nb = w - sb;
-      if (nb > 0 && hr > 0) {
-        const int tot = nb * hr * 2;
-        for (int idx = tid; idx < tot; idx += T) {
-          const int part = idx & 1, rest = idx >> 1;
-          const int s = sb + rest / hr, l = rest % hr;
-          double* ts = tile + (size_t)s * E * h;
-          elem cc;
-#pragma unroll
-          for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
-          elem y = sm_load_part<Ar>(ts, h, l, part);
-          Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
-#pragma unroll
-          for (int q = 0; q < L; ++q) ts[(part * L + q) * h + l] = y.v[part * L + q];
-        }
-      }
+      update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, w - sb);
     }
 
     MGS_TR(k, 4);

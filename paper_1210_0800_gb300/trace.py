@@ -10,8 +10,8 @@ library (lib/trace/), runs a few solves of one size and prints where the time go
 Phases of the grid-barrier kernel, per step k: reduction of the Br partial Gram rows,
 coefficient division, look-ahead update of column k+1, update of the other columns,
 wait for and copy of pivot k+1, partials of step k+1, grid barrier.  Of the cluster
-schedule: phase A (column k+1 on its owner), partials and cluster reduction, coefficient
-division, R/y stores and updates, wait for pivot k+1.
+schedule: phase A (column k+1 on its owner), partials of the other columns, cluster
+barrier and reduction, coefficient division, R/y stores and updates, wait for pivot k+1.
 """
 
 from __future__ import annotations
@@ -24,7 +24,7 @@ import numpy as np
 from . import _binding, build, inputs
 
 GRID_PHASES = ["reduce", "coef", "lookahead", "update", "wait+copy", "partials", "barrier"]
-CLUSTER_PHASES = ["A (column k+1)", "partials+reduce", "coef", "store+update", "wait pivot"]
+CLUSTER_PHASES = ["A (column k+1)", "partials", "sync+reduce", "coef", "store+update", "wait pivot"]
 
 
 def _load_trace_library():
@@ -75,12 +75,18 @@ def summarize(plan, tr) -> str:
         act = row[:, 0] > 0
         if not act.any():
             continue
-        for i in range(len(names)):
-            if grid and i == len(names) - 1:
-                nxt = tr[k + 1, act, 0]
-                tot[i] += np.mean(nxt - row[act, 6])
-            else:
-                tot[i] += np.mean(row[act, i + 1] - row[act, i])
+        if grid:
+            for i in range(len(names)):
+                end = tr[k + 1, act, 0] if i == len(names) - 1 else row[act, i + 1]
+                tot[i] += np.mean(end - row[act, i])
+        else:
+            # stamps 0 start, 1 after A, 6 after the partials (0 where the step had none),
+            # 2 after the cluster reduction, 3 coefficients, 4 updates, 5 pivot received
+            has = row[act, 6] > 0
+            mid = np.where(has, row[act, 6], row[act, 1])
+            b = [row[act, 0], row[act, 1], mid, row[act, 2], row[act, 3], row[act, 4], row[act, 5]]
+            for i in range(len(names)):
+                tot[i] += np.mean(b[i + 1] - b[i])
     t0 = tr[0, :, 0][tr[0, :, 0] > 0].min()
     ep = tr[nc]
     lines.append("sweep %.1f us, solve %.1f us" % ((ep[:, 0].max() - t0) / 1e3, (ep[:, 3].max() - t0) / 1e3))
