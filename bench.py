@@ -430,7 +430,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     if clk:
         line["clocks"] = clk
     if world == 1 and not args.no_cpu_baseline:
-        v, desc, dt = oracle_sample(L, m, n, args.ref_seconds * 4)
+        v, desc, dt = oracle_sample(L, m, n, args.ref_seconds * 6)  # about 12 s of CPU work
         line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": desc}
     print(json.dumps(line))
     return 0
