@@ -659,27 +659,39 @@ __global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
     const int nact = w - first;                // own columns j > k
     MGS_TR(k, 0);
 
-    // (1) reduce the Br partials of the pivot norm and of the own columns j > k, one lane
-    //     per (column, part, row block); a shuffle tree over the row blocks
+    // (1) reduce the Br partials of the pivot norm and of the own columns j > k: g lanes
+    //     per (column, part), lane pp folding row blocks pp, pp + g, ..., then a shuffle
+    //     tree over the g lanes.  g is the largest power of two up to Br that fits the busiest
+    //     CTA's jobs in one round, the same in every CTA, so G_kk is summed in the same
+    //     order everywhere.
     {
       const int BrP = pow2_ceil(Br);
       const int nred = 1 + max(nact, 0);
-      const int jobs = nred * 2 * BrP;
+      const int nact_max = (nc - 1 - k + Bc - 1) / Bc;
+      int g = BrP;
+      while (g > 1 && (1 + nact_max) * 2 * g > T) g >>= 1;
+      const int jobs = nred * 2 * g;
       for (int base = 0; base < jobs; base += T) {
         const int job = base + tid;
-        const int ci = job / (2 * BrP), rem = job % (2 * BrP);
-        const int part = rem / BrP, pp = rem % BrP;
+        const int ci = job / (2 * g), rem = job % (2 * g);
+        const int part = rem / g, pp = rem % g;
         const bool want = job < jobs && !(ci == 0 && part == 1);
         pacc a;
         Ar::pzero(a);
         if (want && pp < Br) {
           const int j = (ci == 0) ? k : col_of(first + ci - 1);
-          const double* src = pr.P + (((size_t)cur * Br + pp) * nc + j) * ACC + part * PACC;
           double* d = reinterpret_cast<double*>(&a);
 #pragma unroll
-          for (int q = 0; q < PACC; ++q) d[q] = __ldcg(src + q);
+          for (int q = 0; q < PACC; ++q) d[q] = __ldcg(pr.P + (((size_t)cur * Br + pp) * nc + j) * ACC + part * PACC + q);
+          for (int qb = pp + g; qb < Br; qb += g) {
+            pacc o;
+            double* od = reinterpret_cast<double*>(&o);
+#pragma unroll
+            for (int q = 0; q < PACC; ++q) od[q] = __ldcg(pr.P + (((size_t)cur * Br + qb) * nc + j) * ACC + part * PACC + q);
+            Ar::pcombine(f, a, o);
+          }
         }
-        for (int off = 1; off < BrP; off <<= 1) {
+        for (int off = 1; off < g; off <<= 1) {
           pacc o;
           const double* sa = reinterpret_cast<const double*>(&a);
           double* so = reinterpret_cast<double*>(&o);
