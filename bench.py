@@ -163,16 +163,16 @@ def peak_fp64_ops_per_s(sm_max_mhz: float) -> float:
 
 
 def kernel_source_sha() -> str:
-    """Hash of the CUDA sources (the ncu traffic figure is valid for this hash only)."""
-    import glob
+    """Hash of the sources of the single-system solver kernels (the ncu traffic figure is
+    valid for this hash only)."""
     import hashlib
 
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1210_0800_gb300", "csrc", "*.cu")) +
-                   glob.glob(os.path.join(ROOT, "paper_1210_0800_gb300", "csrc", "*.cuh")))
+    names = ["ddqd.cuh", "mgs_kernel.cuh", "mgs_cluster.cuh", "launch.cuh", "mgs_d.cu", "mgs_dd.cu", "mgs_qd.cu",
+             "api.cu"]
     h = hashlib.sha256()
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in names:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1210_0800_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -429,6 +429,10 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     }
     if clk:
         line["clocks"] = clk
+    # the FP64 FMA rate measured on this GPU beside the derived peak the roofline uses
+    probe = mg._binding.fp64_probe(blocks=4 * torch.cuda.get_device_properties(dev).multi_processor_count)
+    line["roofline"]["measured_fp64_fma_per_s"] = probe
+    line["roofline"]["measured_over_derived_peak"] = probe / peak_ops
     if world == 1 and not args.no_cpu_baseline:
         v, desc, dt = oracle_sample(L, m, n, args.ref_seconds * 6)  # about 12 s of CPU work
         line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": desc}

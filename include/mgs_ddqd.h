@@ -277,6 +277,16 @@ int newton_step_dd(double* J, int ldj, double* F, double* x, int m, int n, doubl
 int newton_step_qd(double* J, int ldj, double* F, double* x, int m, int n, double tol, mgs_newton_state* dev_state,
                    void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 
+/*
+ * FP64 throughput probe (no counterpart in the paper): launches `blocks` x `threads`
+ * threads, each running 8 independent chains of `iters` fused multiply-adds, and writes
+ * one double per thread to dev_out (blocks * threads doubles).  The caller times the
+ * stream: blocks * threads * iters * 8 FMA lane-operations per launch.  This measures the
+ * rate the roofline of the FP64-bound solve is quoted against.
+ * Host returns: MGS_OK, MGS_EINVAL or MGS_ECUDA.
+ */
+int mgs_fp64_probe(double* dev_out, int blocks, int threads, int iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

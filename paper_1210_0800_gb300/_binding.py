@@ -20,7 +20,7 @@ EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_works
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
            "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
            "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched", "mgs_plan_query",
-           "newton_workspace_bytes", "newton_step_d", "newton_step_dd", "newton_step_qd"]
+           "newton_workspace_bytes", "newton_step_d", "newton_step_dd", "newton_step_qd", "mgs_fp64_probe"]
 
 
 class MgsTune(ctypes.Structure):
@@ -61,6 +61,8 @@ def load(path: str | None = None):
     for name in ("newton_step_d", "newton_step_dd", "newton_step_qd"):
         getattr(lib, name).restype = i
         getattr(lib, name).argtypes = [dp, i, dp, dp, i, i, ctypes.c_double, vp, vp, sz, vp, vp]
+    lib.mgs_fp64_probe.restype = i
+    lib.mgs_fp64_probe.argtypes = [dp, i, i, i, vp]
     lib.mgs_plan_query.restype = i
     lib.mgs_plan_query.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int)]
     qr_args = [dp, i, dp, i, i, i, vp, sz, vp, vp]
@@ -223,6 +225,27 @@ def mgs_qr_qd(A, R=None, workspace=None, status=None, stream=None):
 
 def mgs_workspace_bytes(limbs: int, m: int, n: int, with_rhs: bool = True) -> int:
     return workspace_bytes(limbs, m, n, with_rhs)
+
+
+def fp64_probe(blocks: int, threads: int = 256, iters: int = 4096, reps: int = 5) -> float:
+    """Measured FP64 fused multiply-add lane-operations per second of this GPU (the best of
+    `reps` timed launches of mgs_fp64_probe)."""
+    import torch
+
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc = load().mgs_fp64_probe(_ptr(out), blocks, threads, iters, _stream(st))
+        e1.record(st)
+        if rc != MGS_OK:
+            raise MGSError(rc, "mgs_fp64_probe")
+        torch.cuda.synchronize()
+        if r:  # the first launch warms up
+            best = max(best, blocks * threads * iters * 8 / (e0.elapsed_time(e1) / 1000.0))
+    return best
 
 
 def mgs_plan_query(limbs: int, m: int, n: int, with_rhs: bool = True) -> dict:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBRARY = os.path.join(LIBDIR, "libmgs_ddqd.so")
 HOST_LIBRARY = os.path.join(LIBDIR, "libddqd_host.so")
-SOURCES = ["api.cu", "mgs_d.cu", "mgs_dd.cu", "mgs_qd.cu", "noalloc.cu", "batched.cu", "newton.cu"]
+SOURCES = ["api.cu", "mgs_d.cu", "mgs_dd.cu", "mgs_qd.cu", "noalloc.cu", "batched.cu", "newton.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--fmad=false"]
 # extra nvcc flags for experiments; empty by default
