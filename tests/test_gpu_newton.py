@@ -87,8 +87,9 @@ def test_gate_stops_after_convergence(orc):
     assert rel(orc, x.cpu().numpy(), xs) <= 1e-24
     # the state is the gate: a further step on a converged run changes nothing
     state = mg.NewtonState(dev)
-    state.buf.copy_(torch.from_numpy(np.frombuffer(np.array([1, 5, 0, 0], dtype=np.int32).tobytes() +
-                                                   bytes(mg.newton.STATE_BYTES - 16), dtype=np.uint8)))
+    raw = np.zeros(mg.newton.STATE_BYTES, dtype=np.uint8)
+    raw[:16] = np.array([1, 5, 0, 0], dtype=np.int32).view(np.uint8)
+    state.buf.copy_(torch.from_numpy(raw))
     before = x.clone()
     J = torch.empty(A.shape, dtype=torch.float64, device=dev)
     F = torch.empty(b.shape, dtype=torch.float64, device=dev)
