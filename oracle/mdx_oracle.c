@@ -601,7 +601,11 @@ EXPORT void oracle_matvec(int Lin, const double *A, int m, int n, int lda, const
       cx a = cx_load(ELEM(A, i, j, lda, Lin), Lin);
       cx v = cx_load(x + (size_t)j * 2 * Lin, Lin);
       xp_add_prod(&Er, &a.re, &v.re, Lin, 1.0);
+#if ORACLE_PLANT == 10
+      xp_add_prod(&Er, &a.im, &v.im, Lin, 1.0); /* planted: wrong sign of the im*im term */
+#else
       xp_add_prod(&Er, &a.im, &v.im, Lin, -1.0);
+#endif
       xp_add_prod(&Ei, &a.re, &v.im, Lin, 1.0);
       xp_add_prod(&Ei, &a.im, &v.re, Lin, 1.0);
       if (Er.n > 256) xp_compress(&Er);
@@ -630,7 +634,11 @@ EXPORT void oracle_matvec_conjT(int Lin, const double *A, int m, int n, int lda,
       cx a = cx_load(ELEM(A, i, j, lda, Lin), Lin);
       cx w = cx_load(v + (size_t)i * 2 * Lin, Lin);
       xp_add_prod(&Er, &a.re, &w.re, Lin, 1.0);
+#if ORACLE_PLANT == 9
+      xp_add_prod(&Er, &a.im, &w.im, Lin, -1.0); /* planted: A^T v instead of A^H v */
+#else
       xp_add_prod(&Er, &a.im, &w.im, Lin, 1.0);
+#endif
       xp_add_prod(&Ei, &a.re, &w.im, Lin, 1.0);
       xp_add_prod(&Ei, &a.im, &w.re, Lin, -1.0);
       if (Er.n > 256) xp_compress(&Er);

@@ -414,6 +414,48 @@ def pin_table2(o, prec: str, g: int, count: int, margin: float = 0.5):
     return logs
 
 
+def pin_matvec(o, L: int, Lout: int):
+    """A x and A^H v against exact rational arithmetic: every entry within one rounding to
+    Lout limbs of the exact sum (one row of v is itself a combination of A's columns, so
+    the sums cancel)."""
+    m, n = 7, 5
+    A = inputs.matrix_uniform(m, n, L, 6101)
+    x = inputs.system(m, n, L, 6102)[1]
+    v = inputs.system(m, n, L, 6103)[2]
+    v[3] = o.matvec(A, x)[3]
+    Aex = [[cval(A[j, i]) for j in range(n)] for i in range(m)]
+    xex = [cval(x[j]) for j in range(n)]
+    vex = [cval(v[i]) for i in range(m)]
+    got = o.matvec(A, x, Lout=Lout)
+    gotT = o.matvec_conjT(A, v, Lout=Lout)
+    u = 2.0 ** (-53 * Lout)
+    for i in range(m):
+        want = (sum((cmul(Aex[i][j], xex[j])[0] for j in range(n)), F(0)),
+                sum((cmul(Aex[i][j], xex[j])[1] for j in range(n)), F(0)))
+        g = cval(got[i])
+        for p in range(2):
+            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
+    for j in range(n):
+        want = cdot([Aex[i][j] for i in range(m)], vex)
+        g = cval(gotT[j])
+        for p in range(2):
+            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
+
+
+def pin_matvec_conjT_gram(o):
+    """Q^H q_j from the oracle's own MGS is a column of the identity up to O(kappa u)
+    (Section 3); a transposed instead of conjugated product leaves O(1) cross terms."""
+    A, _, _ = inputs.system(30, 12, 2, 6104)
+    Q, R, st = o.qr(A.copy())
+    assert st == 0
+    for j in (0, 5, 11):
+        col = o.matvec_conjT(Q, Q[j])
+        e = np.zeros_like(col)
+        e[j, 0, 0] = 1.0
+        d, _ = o.max_abs_diff(col, e)
+        assert d < 1e-28
+
+
 def quick_battery(o):
     """Every pin at its smallest size; used on planted builds."""
     pin_error_free_transforms(o)
@@ -424,3 +466,5 @@ def quick_battery(o):
         pin_mgs_special_cases(o, L)
         pin_mgs_exact_rational(o, L, cases=((3, 2), (4, 4)))
     pin_table2(o, "DD", 1, 3)
+    pin_matvec(o, 2, 2)
+    pin_matvec_conjT_gram(o)

@@ -112,45 +112,11 @@ def test_dd_qd_agree(orc):
 
 @pytest.mark.parametrize("L,Lout", [(1, 2), (2, 2), (2, 4), (4, 4)])
 def test_matvec_exact(orc, L, Lout):
-    """A x and A^H v against exact rational arithmetic: every entry within one rounding to
-    Lout limbs of the exact sum (the sums have cancellation: v = A x for some rows)."""
-    m, n = 7, 5
-    A = inputs.matrix_uniform(m, n, L, 6101)
-    x = inputs.system(m, n, L, 6102)[1]
-    v = inputs.system(m, n, L, 6103)[2]
-    v[3] = orc.matvec(A, x)[3]  # a row that is itself a combination of the columns
-    Aex = [[pins.cval(A[j, i]) for j in range(n)] for i in range(m)]
-    xex = [pins.cval(x[j]) for j in range(n)]
-    vex = [pins.cval(v[i]) for i in range(m)]
-    got = orc.matvec(A, x, Lout=Lout)
-    gotT = orc.matvec_conjT(A, v, Lout=Lout)
-    u = 2.0 ** (-53 * Lout)
-    for i in range(m):
-        want = (sum((pins.cmul(Aex[i][j], xex[j])[0] for j in range(n)), pins.F(0)),
-                sum((pins.cmul(Aex[i][j], xex[j])[1] for j in range(n)), pins.F(0)))
-        g = pins.cval(got[i])
-        for p in range(2):
-            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
-    for j in range(n):
-        want = pins.cdot([Aex[i][j] for i in range(m)], vex)
-        g = pins.cval(gotT[j])
-        for p in range(2):
-            assert abs(float(g[p] - want[p])) <= 2 * u * abs(float(want[p])) + 1e-300
+    pins.pin_matvec(orc, L, Lout)
 
 
 def test_matvec_conjT_gram(orc):
-    """Q^H q_j from the oracle's own MGS is a column of the identity up to O(kappa u)
-    (Section 3); a planted transposition (A^T instead of A^H) would leave the imaginary
-    cross terms at O(1)."""
-    A, _, _ = inputs.system(30, 12, 2, 6104)
-    Q, R, st = orc.qr(A.copy())
-    assert st == 0
-    for j in (0, 5, 11):
-        col = orc.matvec_conjT(Q, Q[j])
-        e = np.zeros_like(col)
-        e[j, 0, 0] = 1.0
-        d, _ = orc.max_abs_diff(col, e)
-        assert d < 1e-28
+    pins.pin_matvec_conjT_gram(orc)
 
 
 @pytest.mark.parametrize("L", [2, 4])

@@ -14,6 +14,8 @@ PLANTS = {
     6: "update adds r_kj q_k instead of subtracting",
     7: "rounding never fills the last limb",
     8: "column norm drops the imaginary part",
+    9: "adjoint product A^H v does not conjugate A in the real part",
+    10: "matrix-vector product flips the sign of the imaginary cross term",
 }
 
 
