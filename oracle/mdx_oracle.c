@@ -881,7 +881,11 @@ EXPORT int oracle_ls_adjoint(int L, const double *A, const double *b, const doub
       xp_add_prod(&Ei, &ri.re, &wj.im, L, -1.0);
       /* - g_i conj(x_j) */
       xp_add_prod(&Er, &gi.re, &xj.re, L, -1.0);
+#if ORACLE_PLANT == 11
+      xp_add_prod(&Er, &gi.im, &xj.im, L, 1.0); /* planted: g_i x_j^T instead of g_i x_j^H */
+#else
       xp_add_prod(&Er, &gi.im, &xj.im, L, -1.0);
+#endif
       xp_add_prod(&Ei, &gi.im, &xj.re, L, -1.0);
       xp_add_prod(&Ei, &gi.re, &xj.im, L, 1.0);
       cx o;

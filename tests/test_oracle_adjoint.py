@@ -37,9 +37,8 @@ def exact_adjoint(Aex, bex, Gex):
     return gA, Aw, x
 
 
-@pytest.mark.parametrize("L", [2, 4])
-@pytest.mark.parametrize("m,n", [(3, 3), (4, 4), (5, 3), (6, 4)])
-def test_adjoint_exact_rational(orc, L, m, n):
+def adjoint_exact_pin(orc, L, m, n):
+    """The oracle's gradients on Gaussian-integer systems against exact_adjoint."""
     u = 2.0 ** (-53 * L)
     for rep in range(2):
         seed = 700 + 10 * m + n + rep
@@ -59,6 +58,22 @@ def test_adjoint_exact_rational(orc, L, m, n):
             assert pins.cnorm_inf(pins.csub(pins.cval(gb[i]), eb[i])) <= tol, ("grad_b", i)
             for j in range(n):
                 assert pins.cnorm_inf(pins.csub(pins.cval(gA[j, i]), eA[j][i])) <= tol, ("grad_A", i, j)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("m,n", [(3, 3), (4, 4), (5, 3), (6, 4)])
+def test_adjoint_exact_rational(orc, L, m, n):
+    adjoint_exact_pin(orc, L, m, n)
+
+
+def test_planted_adjoint_mistake_is_caught(tmp_path):
+    """A build whose grad_A uses g x^T instead of g x^H fails the exact pin."""
+    import oracle
+
+    o = oracle.Oracle(oracle.build(plant=11, out=str(tmp_path / "liboracle_plant11.so")))
+    assert o.plant() == 11
+    with pytest.raises(AssertionError):
+        adjoint_exact_pin(o, 2, 4, 4)
 
 
 def loss(orc, A, b):
