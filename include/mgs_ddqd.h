@@ -155,7 +155,8 @@ int ls_solve_qd(double* A, int lda, double* b, double* x, double* R, int ldr, do
  *                        (MGS_OK, MGS_EINVAL for a bad size, MGS_ERANK, MGS_ENONFINITE)
  *   tune                 optional launch shape (NULL or zero fields = defaults)
  * Workspace: mgs_batched_workspace_bytes(limbs, batch, max_m, max_n, tune).
- * One CTA solves one system at a time; no CTA waits for another.
+ * One CTA (or one cluster of `split` CTAs, see mgs_tune) solves one system at a time; no
+ * CTA waits for a CTA outside its own cluster.
  */
 typedef struct {
   int threads;     /* threads per CTA: 128 or 256 (0 = 256) */
@@ -218,7 +219,7 @@ int ls_adjoint_qd_batched(const double* Q_pool, const double* R_pool, const doub
  *   held by every GPU that loads the library until the process exits.  No allocation
  *   routine is called.
  *   Sizes whose workspace (mgs_workspace_bytes(2, m, n, 1)) exceeds the array are rejected
- *   with MGS_ENOSPACE (about n <= 350 for m = n).
+ *   with MGS_ENOSPACE (on GB300, m = n <= 254 with the default kernel choice).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *   with that device current); make it before any stream capture.
  *   Every call shares the array: calls that may overlap on the GPU race and must not be
