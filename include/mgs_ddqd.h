@@ -219,7 +219,7 @@ int ls_adjoint_qd_batched(const double* Q_pool, const double* R_pool, const doub
  *   held by every GPU that loads the library until the process exits.  No allocation
  *   routine is called.
  *   Sizes whose workspace (mgs_workspace_bytes(2, m, n, 1)) exceeds the array are rejected
- *   with MGS_ENOSPACE (on GB300, m = n <= 254 with the default kernel choice).
+ *   with MGS_ENOSPACE (on GB300, m = n <= 346 with the default kernel choice).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *   with that device current); make it before any stream capture.
  *   Every call shares the array: calls that may overlap on the GPU race and must not be

@@ -147,8 +147,8 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, Plan& 
                           : pl.kind == 2 ? mgs::group_partials_doubles(L, pl.Br, pl.Bc, (pl.nc + pl.Bc - 1) / pl.Bc)
                                          : 0;
   off = align256(off + sizeof(double) * pdoubles);
-  pl.off_V = off;  // published pivot rows: one slot per pivot (cluster schedule), two otherwise
-  off = align256(off + sizeof(double) * (size_t)(pl.kind != 0 ? pl.nc + 1 : 2) * pl.Br * pl.h * E);
+  pl.off_V = off;  // published pivot rows: a ring of Bc + 2 slots (cluster schedule), two otherwise
+  off = align256(off + sizeof(double) * (size_t)(pl.kind != 0 ? pl.Bc + 2 : 2) * pl.Br * pl.h * E);
   pl.off_Y = off;
   off = align256(off + sizeof(double) * (size_t)pl.nc * E);
   pl.off_R = off;

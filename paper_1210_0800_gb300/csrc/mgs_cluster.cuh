@@ -88,6 +88,11 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
   const int r0 = p * h;
   const int hr = max(0, min(h, pr.m - r0));
   const int w = (nc - c + Bc - 1) / Bc;
+  // published pivot rows live in a ring of Bc + 2 slots: a cluster that still has to read
+  // pivot j owns a column below j + Bc, and no pivot beyond that column is published before
+  // it has read (the pivots follow one release/acquire chain), so slot j is free again
+  // when pivot j + Bc + 2 is written
+  const int vslots = Bc + 2;
   unsigned epoch = 0, gepoch = 0;
   unsigned* gctr = pr.gsync + (size_t)c * 32;  // this group's arrival counter (HW = false)
   auto group_sync = [&]() {
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
         for (int q = 0; q < E; ++q) pnxt[q * h + l] = 0.0;
       }
       __syncthreads();
-      double* vdst = pr.V + ((size_t)(k + 1) * Br + p) * h * E;
+      double* vdst = pr.V + ((size_t)((k + 1) % vslots) * Br + p) * h * E;
       for (int l = tid; l < h; l += T) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
       __syncthreads();
       if (tid == 0) {
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     if (!own_k1) {
       if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
       __syncthreads();
-      const double* vsrc = pr.V + ((size_t)(k + 1) * Br + p) * h * E;
+      const double* vsrc = pr.V + ((size_t)((k + 1) % vslots) * Br + p) * h * E;
       for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
     }
     __syncthreads();

@@ -58,7 +58,7 @@ struct Params {
   unsigned* gsync;  // per-column-group arrival counters, 32 apart (group kernel)
   int* flags;      // nc * Br pivot-ready flags
   double* P;       // partial Gram rows: 2 * Br * nc * ACC (group kernel: its partial buffers)
-  double* V;       // published pivot rows: 2 * Br * h * 2L
+  double* V;       // published pivot rows: 2 (grid kernel) or Bc + 2 (cluster schedule) slots of Br * h * 2L
   double* Y;       // y = Q^H b (and the back-substitution right-hand side): nc * 2L
   double* Gd;      // pivot norms G_kk = ||a_k||^2: nc * L
   double* Rd;      // r_kk: nc * L
