@@ -584,6 +584,137 @@ def run_gpu_batched(args, rank, world):
 
 
 DIFF = {"c4_dd_diff_160x128x64": (2, 160, 128, 64)}
+# Newton corrector runs: (limbs, m, n, steps per run)
+NEWTON = {"newton_dd_256x256x8": (2, 256, 256, 8), "newton_qd_320x256x8": (4, 320, 256, 8)}
+
+
+def run_gpu_newton(args, rank, world):
+    """One step = one run of gated Newton corrector steps (newton_step_*) on device-resident
+    Jacobians and residuals, as in path tracking with the evaluation on the GPU (the
+    caller's: here copies of pre-generated J_i, F_i), the whole run replayed from one CUDA
+    graph; beside it the same run launched eagerly and the plain solves it contains."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    L, m, n, S = NEWTON[args.workload]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    host = [inputs.system(m, n, L, replica_seed(args.workload, rank, i)) for i in range(S)]
+    Js = [torch.from_numpy(h[0]).to(dev) for h in host]
+    Fs = [torch.from_numpy(h[2]).to(dev) for h in host]
+    x0 = torch.from_numpy(host[0][1]).to(dev)
+    J = torch.empty_like(Js[0])
+    F = torch.empty_like(Fs[0])
+    x = x0.clone()
+    ws = torch.empty(mg.newton.workspace_bytes(L, m, n), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    state = mg.NewtonState(dev)
+
+    def run(stream):
+        for i in range(S):
+            J.copy_(Js[i], non_blocking=True)
+            F.copy_(Fs[i], non_blocking=True)
+            mg.newton_step(J, F, x, 0.0, state, workspace=ws, status=st, stream=stream)
+
+    cur = torch.cuda.current_stream(dev)
+    run(cur)  # first-call set-up outside the capture
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        run(side)
+
+    def replay():
+        x.copy_(x0, non_blocking=True)
+        state.buf.zero_()
+        g.replay()
+
+    for _ in range(W):
+        replay()
+    torch.cuda.synchronize(dev)
+    flush_l2(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(cur)
+    for _ in range(K):
+        replay()
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / K
+    done = state.read()
+    # the same run launched eagerly, and the plain solves alone
+    e0.record(cur)
+    for _ in range(3):
+        x.copy_(x0, non_blocking=True)
+        state.buf.zero_()
+        run(cur)
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    eager_ms = e0.elapsed_time(e1) / 3
+    fn = {1: mg.ls_solve_d, 2: mg.ls_solve_dd, 4: mg.ls_solve_qd}[L]
+    wss = torch.empty(mg.mgs_workspace_bytes(L, m, n, True), dtype=torch.uint8, device=dev)
+    xs = torch.empty_like(x)
+    e0.record(cur)
+    for i in range(S):
+        J.copy_(Js[i], non_blocking=True)
+        F.copy_(Fs[i], non_blocking=True)
+        fn(J, F, x=xs, workspace=wss, status=st)
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    solves_ms = e0.elapsed_time(e1)
+    # end to end: x0 up, the run, the final x and the state down
+    xh = torch.empty_like(x, device="cpu").pin_memory()
+    x0h = x0.cpu().pin_memory()
+    sh = torch.empty_like(state.buf, device="cpu").pin_memory()
+    e0.record(cur)
+    for _ in range(3):
+        x.copy_(x0h, non_blocking=True)
+        state.buf.zero_()
+        g.replay()
+        xh.copy_(x, non_blocking=True)
+        sh.copy_(state.buf, non_blocking=True)
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / 3
+    ms, eager_ms, e2e_ms = max_over_ranks([ms, eager_ms, e2e_ms], dev, world)
+    if rank != 0:
+        return 0
+    ops = S * fp64_ops(L, m, n)
+    peaks = read_peaks()
+    peak_ops = peak_fp64_ops_per_s(float(peaks.get("sm_max_mhz", 2070.0)))
+    line = {
+        "metric": METRIC, "value": world * S / (ms / 1000.0), "unit": "Newton steps/s (one solve each)",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "newton_steps_per_run": S,
+                   "step": "one CUDA-graph replay of %d gated newton_step calls, J and F copied in from device "
+                           "memory before each" % S, "l2": L2_NOTE,
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": world * S / (e2e_ms / 1000.0), "unit": "Newton steps/s",
+                "h2d_bytes_per_step": x0h.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8 + sh.numel()},
+        "gpu_launches": 3 * S * K,
+        "roofline": {"bound": "alu", "achieved": 2 * ops / (ms / 1000.0) / 1e12, "peak": 2 * peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": ops / (ms / 1000.0) / peak_ops, "traffic": None,
+                     "note": "algorithmic FP64 instructions of the solves (%.4g) per run" % ops},
+        "eager_run_ms": eager_ms,
+        "plain_solves_ms": solves_ms,
+        "corrector_overhead": (ms - solves_ms) / solves_ms,
+        "state_after_run": {"done": done["done"], "iterations": done["iterations"]},
+    }
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line))
+    return 0
 
 
 def run_gpu_diff(args, rank, world):
@@ -697,7 +828,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(DIFF))
+    ap.add_argument("--workload", default=DEFAULT,
+                    choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(DIFF) + sorted(NEWTON))
     ap.add_argument("--seq-sample", type=int, default=64, help="systems solved one by one for the comparison")
     ap.add_argument("--ref-seconds", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -714,6 +846,11 @@ def main(argv=None):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    if args.workload in NEWTON:
+        if args.impl == "reference":
+            L, m, n, S = NEWTON[args.workload]
+            return run_reference(args, L, m, n, rank, world)
+        return run_gpu_newton(args, rank, world)
     if args.workload in DIFF:
         if args.impl == "reference":
             L, m, n, B = DIFF[args.workload]
