@@ -27,8 +27,11 @@
  * Concurrency.  A single-system call occupies the whole GPU with one persistent launch
  * of at most one CTA per SM whose CTAs wait for one another (a cooperative launch, or a
  * launch of thread-block clusters whose residency the library checks first); calls on
- * the same stream run one after another.  A workspace must not be shared by calls that
- * may run at the same time.  The first call for a given size and device queries the
+ * the same stream run one after another.  Issue single-system calls on one stream at a
+ * time: a launch that finds SMs occupied by another call's kernel waits for them when it
+ * is cooperative, and a cluster launch captured into a CUDA graph (which cannot carry the
+ * cooperative attribute) would find its waits running out and report MGS_ETIMEOUT rather
+ * than hang.  A workspace must not be shared by calls that may run at the same time.  The first call for a given size and device queries the
  * device (occupancy); make it before capturing calls into a CUDA graph.
  */
 #ifndef MGS_DDQD_H
