@@ -144,3 +144,31 @@ def test_automatic_split_for_small_batches(orc):
         A, b = systems[i]
         Q, r, x = unpack(bt, i, systems)
         assert rel(orc, x, orc.ls_solve(A.copy(), b.copy())["x"]) <= TOL[2]
+
+
+@pytest.mark.parametrize("L,split", [(2, 1), (2, 2), (4, 1), (1, 4)])
+def test_batched_packed_r_vs_oracle(orc, L, split):
+    """The optional packed R of the batched solve (element (k, j), k <= j, at j(j+1)/2 + k;
+    the forward output the adjoint reuses) agrees with the oracle's R, system by system,
+    in one CTA per system and split over a cluster."""
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    systems = ragged(orc, L, 10, 67 + L + split, n_lo=1, n_hi=48, extra_hi=10)
+    bt = mg.make_batch(systems, torch.device("cuda:0")).with_R()
+    st = mg.ls_solve_batched(bt, tune=(256, 1, split)).cpu().numpy()
+    torch.cuda.synchronize()
+    assert (st == 0).all()
+    for i, (A, b) in enumerate(systems):
+        n = A.shape[0]
+        o = orc.ls_solve(A.copy(), b.copy())
+        ro = int(bt.r_off[i])
+        packed = bt.R_pool[ro:ro + n * (n + 1) // 2].cpu().numpy()
+        R = np.zeros_like(o["R"])
+        for j in range(n):
+            R[j, :j + 1] = packed[j * (j + 1) // 2:j * (j + 1) // 2 + j + 1]
+        Ro = o["R"].copy()
+        for j in range(n):
+            Ro[j, j + 1:] = 0.0
+        assert rel(orc, R, Ro) <= TOL[L], i
