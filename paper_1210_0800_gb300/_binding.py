@@ -368,6 +368,8 @@ def ls_adjoint_batched(bt, G_pool, gA_pool=None, gb_pool=None, workspace=None, s
         workspace = torch.empty(256, dtype=torch.uint8, device=dev)
     if status is None:
         status = torch.empty(bt.batch, dtype=torch.int32, device=dev)
+    if bt.limbs not in (2, 4):
+        raise ValueError("the adjoint is built for complex double-double and quad-double (limbs 2 or 4)")
     fn = load().ls_adjoint_dd_batched if bt.limbs == 2 else load().ls_adjoint_qd_batched
     tp = ctypes.byref(MgsTune(*tune)) if tune else None
     rc = fn(_ptr(bt.A_pool), _ptr(bt.R_pool), _ptr(bt.x_pool), _ptr(bt.b_pool), _ptr(G_pool), _ptr(gA_pool),

@@ -67,5 +67,8 @@ class LeastSquares(torch.autograd.Function):
 
 
 def lstsq(A, b, save_budget=DEFAULT_SAVE_BUDGET, tune=None):
-    """Differentiable batched least squares (see LeastSquares)."""
+    """Differentiable batched least squares (see LeastSquares); complex double-double or
+    quad-double (the last dimension of A and b holds 2 or 4 limbs)."""
+    if A.shape[-1] not in (2, 4):
+        raise ValueError("lstsq differentiates double-double and quad-double solves (2 or 4 limbs)")
     return LeastSquares.apply(A, b, save_budget, tune)

@@ -115,3 +115,28 @@ def test_dd_gradient_vs_qd_central_differences(orc):
                 fd = (L_of(solve_qd(A4, bp)) - L_of(solve_qd(A4, bm))) / (2 * F(h))
                 want = sum(F(float(v)) for v in gb[i][ii, part])
             assert abs(float(fd - want)) <= 1e-26 * max(1.0, abs(float(want))), (i, which, float(fd), float(want))
+
+
+@pytest.mark.parametrize("B,m,n", [(2, 18, 12), (2, 30, 24)])
+def test_qd_adjoint_vs_oracle(orc, B, m, n):
+    """The quad-double adjoint (ls_adjoint_qd_batched through lstsq) against the oracle."""
+    A, b = uniform(orc, B, m, n, 4, 7950 + m)
+    x, gA, gb = grads_gpu(A, b)
+    for i in range(B):
+        ox = orc.ls_solve(A[i].copy(), b[i].copy())["x"]
+        oA, ob, _, st = orc.ls_adjoint(A[i], b[i], 2.0 * ox)
+        assert st == 0
+        assert rel(orc, x[i], ox) <= 1e-56
+        assert rel(orc, gA[i], oA) <= 1e-55, i
+        assert rel(orc, gb[i], ob) <= 1e-55, i
+
+
+def test_complex_double_is_refused():
+    import torch
+
+    import paper_1210_0800_gb300 as mg
+
+    A = torch.zeros((1, 3, 4, 2, 1), dtype=torch.float64, device="cuda:0")
+    b = torch.zeros((1, 4, 2, 1), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(ValueError):
+        mg.lstsq(A, b)
