@@ -131,6 +131,8 @@ struct D {
     double s;
   };
   static constexpr int PACC = 1;
+  // FP64 instructions of mac_part and of pcombine (work-mapping choices weigh with them)
+  static constexpr int kMacOps = 2, kCombineOps = 1;
   __host__ __device__ static __forceinline__ void pzero(pacc& a) { a.s = 0.0; }
   // part 0: a += xr yr + xi yi;  part 1: a += xr yi - xi yr
   __host__ __device__ static __forceinline__ void mac_part(const Fp& f, pacc& a, const elem& x, const elem& y,
@@ -232,6 +234,7 @@ struct DD {
     double S, C;
   };
   static constexpr int PACC = 2;
+  static constexpr int kMacOps = 18, kCombineOps = 5;  // mac_part, pcombine
   __host__ __device__ static __forceinline__ void pzero(pacc& a) { a.S = a.C = 0.0; }
   // part 0: a += Re(conj(x) y) = xr yr + xi yi;  part 1: a += Im(conj(x) y) = xr yi - xi yr
   __host__ __device__ static __forceinline__ void mac_part(const Fp& f, pacc& a, const elem& x, const elem& y,
@@ -500,6 +503,7 @@ struct QD {
 
   using pacc = part_t;
   static constexpr int PACC = 4;
+  static constexpr int kMacOps = 140, kCombineOps = 22;  // mac_part, pcombine
   __host__ __device__ static __forceinline__ void pzero(pacc& a) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) a.s[i] = 0.0;
@@ -531,6 +535,25 @@ struct QD {
     }
     prod(f, a, r.v, x1);
     prod(f, a, r2, x2);
+  }
+  // One half of part `part` of a -= r x: half 0 subtracts the product rr x_part, half 1
+  // the cross term (ri xi for the real part, ri xr for the imaginary part); the two halves
+  // run on two lanes and are merged, which halves a dependent update chain.
+  __host__ __device__ static __forceinline__ void mul_sub_half(const Fp& f, pacc& a, const elem& r, const elem& x,
+                                                              int part, int half) {
+    const bool im = part != 0, h1 = half != 0;
+    double u[4], v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      u[i] = h1 ? flip_if(r.v[4 + i], im) : -r.v[i];
+      v[i] = (im != h1) ? x.v[4 + i] : x.v[i];
+    }
+    prod(f, a, u, v);
+  }
+  // An accumulator holding the normalised value y (L limbs).
+  __host__ __device__ static __forceinline__ void pseed(pacc& a, const double* y) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.s[i] = y[i];
   }
   __host__ __device__ static __forceinline__ void pcombine(const Fp& f, pacc& a, const pacc& b) { merge(f, a, b); }
   __host__ __device__ static __forceinline__ void pfinal(const Fp& f, const pacc& a, double* o) { renorm(f, a, o); }

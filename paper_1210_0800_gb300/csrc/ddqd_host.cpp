@@ -146,3 +146,19 @@ EXPORT void h_axpy_parts(int L, int n, const double* y, const double* r, const d
   else
     axpy_parts<mgs::QD>(n, y, r, x, out);
 }
+// out = y - c x (QD) as the back substitution's chain forms it: each part is split over
+// two accumulators (the seeded one takes the product c_re x_part, the other the cross
+// term), merged and renormalised.
+EXPORT void h_update_split_qd(const double* y, const double* c, const double* x, double* out) {
+  using Q = mgs::QD;
+  const auto cc = load<Q>(c), xx = load<Q>(x);
+  for (int part = 0; part < 2; ++part) {
+    Q::pacc a, b;
+    Q::pseed(a, y + part * 4);
+    Q::mul_sub_half(kFp, a, cc, xx, part, 0);
+    Q::pzero(b);
+    Q::mul_sub_half(kFp, b, cc, xx, part, 1);
+    Q::pcombine(kFp, a, b);
+    Q::pfinal(kFp, a, out + part * 4);
+  }
+}

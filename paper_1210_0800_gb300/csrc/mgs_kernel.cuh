@@ -243,6 +243,24 @@ __device__ __forceinline__ typename Ar::acc acc_shfl_xor(const typename Ar::acc&
 
 __device__ __forceinline__ int pow2_floor(int v) { return v <= 1 ? 1 : 1 << (31 - __clz(v)); }
 __device__ __forceinline__ int pow2_ceil(int v) { return v <= 1 ? 1 : 1 << (32 - __clz(v - 1)); }
+__device__ __forceinline__ int ceil_log2(int v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
+
+// Partials of one step: `pairs` (column, part) dot products over hr rows.  The strided
+// mapping gives each pair C lanes (rows ch, ch + C, ...) and a tree of log2 C levels;
+// the flat mapping gives every lane the same number of consecutive (pair, row) items.
+// A warp pays for every FP64 instruction whatever its active lanes, so the mapping with
+// fewer products plus combines on the busiest lane wins.  The flat one needs a lane's
+// items to span at most two pairs, i.e. pairs <= T.
+template <class Ar, int T>
+__device__ __forceinline__ bool flat_partials_cheaper(int pairs, int hr, int C) {
+  if (pairs > T || hr < 1) return false;
+  const int per_round = T / C;
+  const int rounds = (pairs + per_round - 1) / per_round;
+  const int strided = rounds * (((hr + C - 1) / C) * Ar::kMacOps + ceil_log2(C) * Ar::kCombineOps);
+  const int per = (pairs * hr + T - 1) / T;
+  const int flat = per * Ar::kMacOps + (ceil_log2((hr + per - 1) / per) + 1) * Ar::kCombineOps;
+  return flat < strided;
+}
 
 // a_j -= c_j p for the tile slots [sb, sb + nb) over the CTA's hr rows (c_j at
 // coef + slot * 2L, the pivot rows in piv).  For D and DD with at least two elements per
@@ -445,13 +463,40 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
 #pragma unroll
         for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
         if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
-        for (int t = tid; t < 2 * (k - s); t += T) {
-          const int j = s + (t >> 1), part = t & 1;
-          double* yj = ys + (size_t)(j - s) * E;
-          elem y = sm_load_part<Ar>(yj, 1, 0, part);
-          Ar::update_part(f, y, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (j - s)) * E, 1, 0), xk, part);
+        if constexpr (L == 4) {
+          // QD: the two products of each part go to two adjacent lanes (the first seeded
+          // with y_j), which merge through a shuffle: a chain link of one product, a merge
+          // and a renormalisation instead of two products and a renormalisation.  The
+          // 4 (k - s) lanes fit one pass; every lane of a warp takes part in the shuffle.
+          static_assert(4 * (kBS - 1) <= T, "one pass of the split chain");
+          const int t = tid;
+          const bool act = t < 4 * (k - s);
+          const int j = s + (t >> 2), part = (t >> 1) & 1, half = t & 1;
+          double* yj = ys + (size_t)(act ? j - s : 0) * E;
+          pacc a;
+          Ar::pzero(a);
+          if (act) {
+            if (half == 0) Ar::pseed(a, yj + part * L);
+            Ar::mul_sub_half(f, a, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (j - s)) * E, 1, 0), xk, part, half);
+          }
+          pacc o;
+          const double* sa = reinterpret_cast<const double*>(&a);
+          double* so = reinterpret_cast<double*>(&o);
 #pragma unroll
-          for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
+          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], 1);
+          if (act && half == 0) {
+            Ar::pcombine(f, a, o);
+            Ar::pfinal(f, a, yj + part * L);
+          }
+        } else {
+          for (int t = tid; t < 2 * (k - s); t += T) {
+            const int j = s + (t >> 1), part = t & 1;
+            double* yj = ys + (size_t)(j - s) * E;
+            elem y = sm_load_part<Ar>(yj, 1, 0, part);
+            Ar::update_part(f, y, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (j - s)) * E, 1, 0), xk, part);
+#pragma unroll
+            for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
+          }
         }
         __syncthreads();
       }
@@ -608,6 +653,68 @@ __global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
     C = max(1, min(C, max(hr, 1)));
     const int per_round = T / C;
     pacc* red = reinterpret_cast<pacc*>(redb);
+    if (flat_partials_cheaper<Ar, T>(pairs, hr, C)) {
+      // Flat mapping: the pairs * hr (pair, row) items in order, `per` consecutive items per
+      // lane, so every lane does the same number of products.  A lane whose items run
+      // into the next pair keeps a second accumulator (in the coefficient area, dead
+      // during the partials).  The lanes starting in one pair combine by a tree rooted at
+      // the first of them, which then folds in the second accumulator of the lane before.
+      const int items = pairs * hr;
+      const int per = (items + T - 1) / T;
+      const int lev = ceil_log2((hr + per - 1) / per);
+      pacc* carry = reinterpret_cast<pacc*>(coef);  // one slot per pair (w E doubles = 2w pacc)
+      const int st = tid * per, en = min(st + per, items);
+      const bool act = st < items;
+      const int p0 = act ? st / hr : 0;
+      const int fl = (p0 * hr + per - 1) / per;                   // first lane starting in pair p0
+      const int cnt = (min((p0 + 1) * hr, items) - 1) / per - fl + 1;  // lanes starting in pair p0
+      // One loop of `per` iterations for every lane (two loops, one per pair, would run one
+      // after the other in a warp that holds a lane crossing a pair boundary).  The pivot
+      // column's imaginary part is computed like any other and written as zero.
+      const int bnd = min(en, (p0 + 1) * hr);
+      const bool cross = act && en > bnd;  // this lane's items run into pair p0 + 1
+      pacc a, cur;
+      Ar::pzero(a);
+      Ar::pzero(cur);
+      for (int it = 0; it < per; ++it) {
+        const int i = st + it;
+        if (cross && i == bnd) {  // keep the first pair's sum, start the second
+          a = cur;
+          Ar::pzero(cur);
+        }
+        const int pp = i < bnd ? p0 : p0 + 1;
+        const int s = first + (pp >> 1), part = pp & 1, l = i - pp * hr;
+        if (i < en) Ar::mac_part(f, cur, sm_load<Ar>(pivbuf, h, l), sm_load<Ar>(tile + (size_t)s * E * h, h, l), part);
+      }
+      if (cross) {
+        carry[p0 + 1] = cur;
+      } else {
+        a = cur;
+      }
+      red[tid] = a;
+      __syncthreads();
+      const int idx = tid - fl;
+      for (int stp = 1; stp < (1 << lev); stp <<= 1) {
+        if (act && (idx % (2 * stp)) == 0 && idx + stp < cnt) {
+          pacc x = red[tid];
+          Ar::pcombine(f, x, red[tid + stp]);
+          red[tid] = x;
+        }
+        __syncthreads();
+      }
+      if (act && idx == 0) {
+        pacc x = red[tid];
+        if (st != p0 * hr) Ar::pcombine(f, x, carry[p0]);  // lane tid - 1 ran into this pair
+        const int j = col_of(first + (p0 >> 1));
+        if (j == kp && (p0 & 1)) Ar::pzero(x);
+        const double* src = reinterpret_cast<const double*>(&x);
+        double* dst = pr.P + (((size_t)buf * Br + p) * nc + j) * ACC + (p0 & 1) * PACC;
+#pragma unroll
+        for (int q = 0; q < PACC; ++q) dst[q] = src[q];
+      }
+      __syncthreads();
+      return;
+    }
     for (int base = 0; base < pairs; base += per_round) {
       const int job = tid / C, ch = tid % C;
       const int pi = base + job;

@@ -29,6 +29,7 @@ def hl():
     lib.h_two_prod.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp]
     lib.h_dot_parts.argtypes = [i, i, i, dp, dp, dp]
     lib.h_axpy_parts.argtypes = [i, i, dp, dp, dp, dp]
+    lib.h_update_split_qd.argtypes = [dp, dp, dp, dp]
     return lib
 
 
@@ -123,6 +124,28 @@ def test_update(hl, L):
         _, xp = P(x)
         oa, op = P(out)
         hl.h_update(L, yp, cp, xp, op)
+        cy, cc, cxv = pins.cval(y), pins.cval(c), pins.cval(x)
+        ex = pins.csub(cy, pins.cmul(cc, cxv))
+        scale = math.sqrt(float(pins.cabs2(cy))) + math.sqrt(float(pins.cabs2(cc)) * float(pins.cabs2(cxv)))
+        assert pins.cnorm_inf(pins.csub(pins.cval(oa), ex)) <= 4 * U[L] * scale
+
+
+def test_update_split_qd(hl):
+    """y - c x with each part's two products on two accumulators that are then merged (the
+    back-substitution chain's form), including near-cancellation."""
+    L = 4
+    ys, cs, xs = cplx(L, 511, 200), cplx(L, 512, 200), cplx(L, 513, 200)
+    for k in range(0, 200, 10):
+        p = pins.cmul(pins.cval(cs[k]), pins.cval(xs[k]))
+        ys[k, 0, 0], ys[k, 1, 0] = float(p[0]), float(p[1])
+        ys[k, :, 1:] = 0.0
+    out = np.zeros((2, L))
+    for y, c, x in zip(ys, cs, xs):
+        _, yp = P(y)
+        _, cp = P(c)
+        _, xp = P(x)
+        oa, op = P(out)
+        hl.h_update_split_qd(yp, cp, xp, op)
         cy, cc, cxv = pins.cval(y), pins.cval(c), pins.cval(x)
         ex = pins.csub(cy, pins.cmul(cc, cxv))
         scale = math.sqrt(float(pins.cabs2(cy))) + math.sqrt(float(pins.cabs2(cc)) * float(pins.cabs2(cxv)))
