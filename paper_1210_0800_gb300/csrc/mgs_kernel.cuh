@@ -893,10 +893,31 @@ __global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
     }
 
     MGS_TR(k, 3);
-    // (4) update the other own columns j > k+1
+    // (4) update the other own columns j > k+1.  A CTA that does not own column k+1 reads
+    //     the pivot-ready flag before its second-to-last column (by then the owners, who
+    //     updated column k+1 first, have usually published it) and, when it was set, loads
+    //     its row of the new pivot into registers before the last column: the two memory
+    //     latencies of step (6) then pass under the updates.  Each thread takes the flag
+    //     with its own acquire load, which orders its reads of the pivot rows.
+    const int* flag1 = pr.flags + (size_t)(k + 1) * Br + p;
+    const double* vsrc = pr.V + ((size_t)nxt * Br + p) * h * E;
+    bool have = false;  // this thread's pivot row (row tid when tid < h) is in pv
+    elem pv;
     {
       const int sb = own_k1 ? first + 1 : first;  // slot of column k+1 is `first` when owned
-      update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, w - sb);
+      const int nb = w - sb;
+      if (!own_k1 && !last && nb >= 3 && T >= h) {
+        update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, nb - 2);
+        const int fv = ld_acquire_s32(flag1);  // first used after the next column
+        update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb + nb - 2, 1);
+        if (fv != 0) {
+          if (tid < h) pv = g_load_cg<Ar>(vsrc + (size_t)tid * E);
+          have = true;
+        }
+        update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb + nb - 1, 1);
+      } else {
+        update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, nb);
+      }
     }
 
     MGS_TR(k, 4);
@@ -916,12 +937,16 @@ __global__ void __launch_bounds__(T, 1) mgs_ls_kernel(Params pr) {
 
     if (last) break;  // plain QR: every column has been reduced
 
-    // (6) the new pivot rows for the CTAs that do not own column k+1
+    // (6) the new pivot rows for the CTAs that do not own column k+1 (prefetched in (4)
+    //     when every thread saw the flag set)
     if (!own_k1) {
-      if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
-      __syncthreads();
-      const double* vsrc = pr.V + ((size_t)nxt * Br + p) * h * E;
-      for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+      if (__syncthreads_and(have)) {
+        if (tid < h) sm_store<Ar>(pnxt, h, tid, pv);
+      } else {
+        if (tid == 0) wait_flag(pr, flag1);
+        __syncthreads();
+        for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+      }
     }
     __syncthreads();
 
