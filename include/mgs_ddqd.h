@@ -291,6 +291,21 @@ int newton_step_qd(double* J, int ldj, double* F, double* x, int m, int n, doubl
  */
 int mgs_fp64_probe(double* dev_out, int blocks, int threads, int iters, void* stream);
 
+/* Failure-detection probe (no counterpart in the paper): runs one of the solver kernels'
+ * bounded waits on a condition that never comes true, so that it runs out of time and
+ * takes the same exit a solve takes when a CTA goes missing.
+ *   kind 0: the pivot-ready flag wait, on a flag nothing sets (one CTA);
+ *   kind 1: the grid barrier, with one of two CTAs never arriving.
+ * dev_words: 4 caller-owned, caller-zeroed device words (4-byte aligned):
+ *   [0] arrival counter, [1] abort flag, [2] status, [3] the flag of kind 0.
+ * After the kernel: [2] = MGS_ETIMEOUT and [1] = 1 once timeout_ns nanoseconds have
+ * passed.  A caller that sets [1] = 1 before the call (an abort raised earlier) sees the
+ * wait fall through at once, [2] unchanged.  The GPU context stays usable either way.
+ * Stream-ordered, asynchronous.  Host returns: MGS_OK, MGS_EINVAL (null or misaligned
+ * words, kind not 0 or 1, timeout_ns outside [1, 1e10]) or MGS_ECUDA.
+ */
+int mgs_wait_probe(unsigned* dev_words, int kind, long long timeout_ns, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ from ._binding import (  # noqa: F401
     mgs_qr_dd,
     mgs_qr_qd,
     mgs_plan_query,
+    mgs_wait_probe,
     mgs_workspace_bytes,
 )
 from .autograd import LeastSquares, lstsq  # noqa: F401,E402

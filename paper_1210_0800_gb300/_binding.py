@@ -20,7 +20,8 @@ EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_works
            "mgs_qr_dd", "mgs_qr_qd", "ls_solve_dd", "ls_solve_qd", "ls_solve_dd_noalloc",
            "mgs_batched_workspace_bytes", "ls_solve_dd_batched", "ls_solve_qd_batched",
            "ls_adjoint_dd_batched", "ls_adjoint_qd_batched", "mgs_qr_d", "ls_solve_d", "ls_solve_d_batched", "mgs_plan_query",
-           "newton_workspace_bytes", "newton_step_d", "newton_step_dd", "newton_step_qd", "mgs_fp64_probe"]
+           "newton_workspace_bytes", "newton_step_d", "newton_step_dd", "newton_step_qd", "mgs_fp64_probe",
+           "mgs_wait_probe"]
 
 
 class MgsTune(ctypes.Structure):
@@ -63,6 +64,8 @@ def load(path: str | None = None):
         getattr(lib, name).argtypes = [dp, i, dp, dp, i, i, ctypes.c_double, vp, vp, sz, vp, vp]
     lib.mgs_fp64_probe.restype = i
     lib.mgs_fp64_probe.argtypes = [dp, i, i, i, vp]
+    lib.mgs_wait_probe.restype = i
+    lib.mgs_wait_probe.argtypes = [vp, i, ctypes.c_longlong, vp]
     lib.mgs_plan_query.restype = i
     lib.mgs_plan_query.argtypes = [i, i, i, i, ctypes.POINTER(ctypes.c_int)]
     qr_args = [dp, i, dp, i, i, i, vp, sz, vp, vp]
@@ -246,6 +249,23 @@ def fp64_probe(blocks: int, threads: int = 256, iters: int = 4096, reps: int = 5
         if r:  # the first launch warms up
             best = max(best, blocks * threads * iters * 8 / (e0.elapsed_time(e1) / 1000.0))
     return best
+
+
+def mgs_wait_probe(words, kind: int, timeout_s: float) -> float:
+    """Run one of the solver's bounded waits until it runs out (kind 0: the pivot-flag wait,
+    kind 1: the grid barrier; `words`: 4 int32 device words, see the C header); returns the
+    kernel's duration in seconds (CUDA events).  The status is left in words[2]."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rc = load().mgs_wait_probe(_ptr(words), int(kind), int(timeout_s * 1e9), _stream(st))
+    e1.record(st)
+    if rc != MGS_OK:
+        raise MGSError(rc, "mgs_wait_probe")
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
 
 
 def mgs_plan_query(limbs: int, m: int, n: int, with_rhs: bool = True) -> dict:

@@ -37,12 +37,12 @@ __device__ __forceinline__ void group_barrier(const Params& pr, unsigned* ctr, u
     ++gepoch;
     const unsigned target = gepoch * (unsigned)members;
     __threadfence();
-    atomicAdd(ctr, 1u);
-    if (!ld_acquire_u32(&pr.sync[1])) {
+    const unsigned arrived = atomicAdd(ctr, 1u) + 1u;
+    if (arrived < target) {  // the last member to arrive does not poll
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
       while (ld_acquire_u32(ctr) < target) {
-        if ((++spins & 255u) == 0) {
+        if ((++spins & 63u) == 0) {
           if (ld_acquire_u32(&pr.sync[1])) break;
           if ((long long)(globaltimer() - t0) > pr.timeout_ns) {
             set_status(pr.status, ST_ETIMEOUT);

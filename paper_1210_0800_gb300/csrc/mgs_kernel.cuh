@@ -119,22 +119,27 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 
 // Grid-wide barrier on a monotone arrival counter.  Returns after all CTAs arrived, or
 // after the abort flag is seen, or after the time limit (then it raises the abort flag).
+// The last CTA to arrive learns it from its own atomic and does not poll; the others poll
+// the counter alone and look at the abort flag and the clock every 64 polls, so the
+// common path costs one memory round trip per poll.
 __device__ __forceinline__ void grid_barrier(const Params& pr, unsigned& epoch) {
   __syncthreads();
   if (threadIdx.x == 0) {
     ++epoch;
     const unsigned target = epoch * gridDim.x;
     __threadfence();
-    atomicAdd(&pr.sync[0], 1u);
-    if (!ld_acquire_u32(&pr.sync[1])) {
+    const unsigned arrived = atomicAdd(&pr.sync[0], 1u) + 1u;
+    if (arrived < target) {
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
       while (ld_acquire_u32(&pr.sync[0]) < target) {
-        if (ld_acquire_u32(&pr.sync[1])) break;
-        if ((++spins & 255u) == 0 && (long long)(globaltimer() - t0) > pr.timeout_ns) {
-          set_status(pr.status, ST_ETIMEOUT);
-          atomicExch(&pr.sync[1], 1u);
-          break;
+        if ((++spins & 63u) == 0) {
+          if (ld_acquire_u32(&pr.sync[1])) break;
+          if ((long long)(globaltimer() - t0) > pr.timeout_ns) {
+            set_status(pr.status, ST_ETIMEOUT);
+            atomicExch(&pr.sync[1], 1u);
+            break;
+          }
         }
       }
     }
@@ -143,13 +148,13 @@ __device__ __forceinline__ void grid_barrier(const Params& pr, unsigned& epoch) 
   __syncthreads();
 }
 
-// Wait until flags[i] != 0 (bounded).  Called by one thread.
+// Wait until flags[i] != 0 (bounded).  Called by one thread.  The flag is polled alone;
+// the abort flag and the clock are looked at every 64 polls.
 __device__ __forceinline__ void wait_flag(const Params& pr, const int* flag) {
-  if (ld_acquire_u32(&pr.sync[1])) return;
   const unsigned long long t0 = globaltimer();
   unsigned spins = 0;
   while (ld_acquire_s32(flag) == 0) {
-    if ((++spins & 255u) == 0) {
+    if ((++spins & 63u) == 0) {
       if (ld_acquire_u32(&pr.sync[1])) return;
       if ((long long)(globaltimer() - t0) > pr.timeout_ns) {
         set_status(pr.status, ST_ETIMEOUT);
@@ -503,10 +508,13 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     }
     if (s == 0) break;
     grid_barrier(pr, epoch);
-    // rows j < s: y_j -= sum_{k in [s, e)} t_jk x~_k; 8 lanes per (row, part) each sum a
-    // share of the terms, a shuffle tree combines them, lane 0 of the group subtracts
+    // rows j < s: y_j -= sum_{k in [s, e)} t_jk x~_k; G lanes per (row, part) each sum a
+    // share of the terms, a shuffle tree combines them, lane 0 of the group subtracts.  G is
+    // the largest of 32, 16, 8 whose lanes the grid holds in one pass (fewest products per
+    // lane), else 8.
     {
-      constexpr int G = 8;
+      int G = 32;
+      while (G > 8 && s * 2 * G > nthreads) G >>= 1;
       const int tot = s * 2 * G;
       const int span = ((tot + nthreads - 1) / nthreads) * nthreads;  // uniform trip count
       for (int idx = gtid; idx < span; idx += nthreads) {

@@ -1,10 +1,18 @@
+// Two probes with no counterpart in the paper.
+//
 // FP64 FMA throughput probe: the rate the roofline of the FP64-bound solve divides by.
 // Every thread runs eight independent multiply-add chains (enough independent work to keep
 // the FP64 unit of its SM sub-partition busy); the result is written so that nothing can be
-// elided.  No counterpart in the paper.
+// elided.
+//
+// Wait probe: one of the solver kernels' bounded waits (the pivot-flag wait, the grid
+// barrier) on a condition that never comes true, so that it runs out of time; the host
+// then reads the status and the abort flag the wait left.  Failure detection is checked
+// this way without faulting or hanging the GPU.
 #include <cuda_runtime.h>
 
 #include "../../include/mgs_ddqd.h"
+#include "mgs_kernel.cuh"
 
 namespace {
 
@@ -23,7 +31,29 @@ __global__ void fp64_fma_probe(double* out, int iters, double a, double b) {
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
+// words: [0] arrival counter, [1] abort flag, [2] status, [3] a flag nothing sets.
+__global__ void wait_probe_kernel(unsigned* words, int kind, long long timeout_ns) {
+  mgs::Params pr{};
+  pr.sync = words;
+  pr.status = reinterpret_cast<int*>(words + 2);
+  pr.timeout_ns = timeout_ns;
+  if (kind == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) mgs::wait_flag(pr, reinterpret_cast<const int*>(words + 3));
+  } else if (blockIdx.x == 0) {  // kind 1: CTA 1 of 2 never arrives at the barrier
+    unsigned epoch = 0;
+    mgs::grid_barrier(pr, epoch);
+  }
+}
+
 }  // namespace
+
+extern "C" int mgs_wait_probe(unsigned* dev_words, int kind, long long timeout_ns, void* stream) {
+  if (!dev_words || (reinterpret_cast<uintptr_t>(dev_words) & 3u) || (kind != 0 && kind != 1) || timeout_ns < 1 ||
+      timeout_ns > 10000000000LL)
+    return MGS_EINVAL;
+  wait_probe_kernel<<<kind == 0 ? 1 : 2, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(dev_words, kind, timeout_ns);
+  return cudaGetLastError() == cudaSuccess ? MGS_OK : MGS_ECUDA;
+}
 
 extern "C" int mgs_fp64_probe(double* dev_out, int blocks, int threads, int iters, void* stream) {
   if (!dev_out || blocks < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1) return MGS_EINVAL;

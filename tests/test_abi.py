@@ -88,3 +88,17 @@ def test_host_argument_checks_newton_and_batched(lib):
     assert L.ls_solve_dd_batched(*bargs(0, 4, 4, good)) == 1           # empty batch
     assert L.ls_solve_qd_batched(*bargs(8, 3, 4, good)) == 1           # max_m < max_n
     assert L.ls_solve_d_batched(*bargs(8, 4, 4, vp(4104))) == 1        # misaligned pool
+
+
+def test_host_argument_checks_wait_probe(lib):
+    """The wait probe rejects bad arguments on the host, before any CUDA call."""
+    from paper_1210_0800_gb300 import _binding
+
+    L = _binding.load()
+    vp = ctypes.c_void_p
+    good, st = vp(4096), vp(8192)
+    assert L.mgs_wait_probe(None, 0, 1000, st) == 1          # null words
+    assert L.mgs_wait_probe(vp(4098), 0, 1000, st) == 1      # misaligned words
+    assert L.mgs_wait_probe(good, 2, 1000, st) == 1          # unknown kind
+    assert L.mgs_wait_probe(good, 1, 0, st) == 1             # no time limit
+    assert L.mgs_wait_probe(good, 0, 20 * 10 ** 9, st) == 1  # above 10 s
