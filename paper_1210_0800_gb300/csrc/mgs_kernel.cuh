@@ -441,6 +441,34 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
     }
   }
   grid_barrier(pr, epoch);
+  if constexpr (L == 4) {
+    // QD: within each diagonal block the unknowns go in pairs (k, k-1), k = e-1, e-3, ...
+    // The lower row of a pair is replaced by itself minus t_{k-1,k} times the upper row,
+    // which eliminates t_{k-1,k}: s_{k-1,m} = t_{k-1,m} - t_{k-1,k} t_{k,m} for m > k in
+    // the block (written over t_{k-1,m}; every operand is an entry this pass leaves alone).
+    // The chain then yields two unknowns per link (see below).
+    const int nblk = (n + kBS - 1) / kBS;
+    const long long tot = (long long)nblk * kBS * kBS * 2;
+    for (long long idx = gtid; idx < tot; idx += nthreads) {
+      const int part = (int)(idx & 1);
+      const long long r = idx >> 1;
+      const int mm = (int)(r % kBS), jj = (int)((r / kBS) % kBS), bk = (int)(r / ((long long)kBS * kBS));
+      const int e = n - bk * kBS, sb = max(0, e - kBS), nbk = e - sb;
+      if (jj >= nbk || mm >= nbk || mm < jj + 2 || ((nbk - jj) & 1)) continue;
+      const int j = sb + jj, m = sb + mm;
+      double* dst = pr.Rt + ((size_t)m * n + j) * E;
+      elem t;
+#pragma unroll
+      for (int q = 0; q < E; ++q) t.v[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < L; ++q) t.v[part * L + q] = __ldcg(dst + part * L + q);
+      Ar::update_part(f, t, g_load_cg<Ar>(pr.Rt + ((size_t)(j + 1) * n + j) * E),
+                      g_load_cg<Ar>(pr.Rt + ((size_t)m * n + j + 1) * E), part);
+#pragma unroll
+      for (int q = 0; q < L; ++q) dst[part * L + q] = t.v[part * L + q];
+    }
+    grid_barrier(pr, epoch);
+  }
   MGS_TR(nc, 2);
   // blocks of kBS rows: CTA 0 runs the chain of the diagonal block (its t_jk staged in
   // shared memory), then every CTA applies the block's x~ to the rows above it.
@@ -463,26 +491,62 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
         for (int q = 0; q < E; ++q) tb[((size_t)kk * kBS + jj) * E + q] = v.v[q];
       }
       __syncthreads();
-      for (int k = e - 1; k >= s; --k) {
-        elem xk;
-#pragma unroll
-        for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
-        if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
-        if constexpr (L == 4) {
-          // QD: the two products of each part go to two adjacent lanes (the first seeded
-          // with y_j), which merge through a shuffle: a chain link of one product, a merge
-          // and a renormalisation instead of two products and a renormalisation.  The
-          // 4 (k - s) lanes fit one pass; every lane of a warp takes part in the shuffle.
-          static_assert(4 * (kBS - 1) <= T, "one pass of the split chain");
+      if constexpr (L == 4) {
+        // QD, pairs (k, k-1): first w_{k-1} = y_{k-1} - t_{k-1,k} y_k for every pair (the
+        // lower rows' coefficients are the eliminated s_{k-1,m}).  A link then takes
+        // x~_k = y_k and x~_{k-1} = w_{k-1} together and subtracts both terms from every
+        // row below: per row and part one lane per term (two QD products, the first lane
+        // seeded with y_j), merged through a shuffle.  Half the links of the one-unknown
+        // chain, each about 183 FP64 instructions instead of 2 x 113.
+        static_assert(4 * (kBS - 2) <= T, "one pass of a pair link");
+        const int np = nbk / 2;
+        {
           const int t = tid;
-          const bool act = t < 4 * (k - s);
+          const bool act = t < 4 * np;
+          const int pi = t >> 2, part = (t >> 1) & 1, half = t & 1;
+          const int k = e - 1 - 2 * pi;
+          double* yw = ys + (size_t)(act ? k - 1 - s : 0) * E;
+          pacc a;
+          Ar::pzero(a);
+          if (act) {
+            if (half == 0) Ar::pseed(a, yw + part * L);
+            Ar::mul_sub_half(f, a, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (k - 1 - s)) * E, 1, 0),
+                             sm_load<Ar>(ys + (size_t)(k - s) * E, 1, 0), part, half);
+          }
+          pacc o;
+          const double* sa = reinterpret_cast<const double*>(&a);
+          double* so = reinterpret_cast<double*>(&o);
+#pragma unroll
+          for (int q = 0; q < PACC; ++q) so[q] = __shfl_xor_sync(0xffffffffu, sa[q], 1);
+          if (act && half == 0) {
+            Ar::pcombine(f, a, o);
+            Ar::pfinal(f, a, yw + part * L);
+          }
+          __syncthreads();
+        }
+        for (int k = e - 1; k - 1 >= s; k -= 2) {
+          elem xk, xk1;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            xk.v[q] = ys[(size_t)(k - s) * E + q];
+            xk1.v[q] = ys[(size_t)(k - 1 - s) * E + q];
+          }
+          if (tid < 2 * E) pr.x[(size_t)(k - 1) * E + tid] = ys[(size_t)(k - 1 - s) * E + tid];
+          const int t = tid;
+          const bool act = t < 4 * (k - 1 - s);
           const int j = s + (t >> 2), part = (t >> 1) & 1, half = t & 1;
           double* yj = ys + (size_t)(act ? j - s : 0) * E;
           pacc a;
           Ar::pzero(a);
           if (act) {
             if (half == 0) Ar::pseed(a, yj + part * L);
-            Ar::mul_sub_half(f, a, sm_load<Ar>(tb + ((size_t)(k - s) * kBS + (j - s)) * E, 1, 0), xk, part, half);
+            const int kk = half == 0 ? k : k - 1;
+            const elem c = sm_load<Ar>(tb + ((size_t)(kk - s) * kBS + (j - s)) * E, 1, 0);
+            elem xv;
+#pragma unroll
+            for (int q = 0; q < E; ++q) xv.v[q] = half == 0 ? xk.v[q] : xk1.v[q];
+            Ar::mul_sub_half(f, a, c, xv, part, 0);
+            Ar::mul_sub_half(f, a, c, xv, part, 1);
           }
           pacc o;
           const double* sa = reinterpret_cast<const double*>(&a);
@@ -493,7 +557,15 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
             Ar::pcombine(f, a, o);
             Ar::pfinal(f, a, yj + part * L);
           }
-        } else {
+          __syncthreads();
+        }
+        if ((nbk & 1) && tid < E) pr.x[(size_t)s * E + tid] = ys[tid];  // an odd block's last unknown
+      } else {
+        for (int k = e - 1; k >= s; --k) {
+          elem xk;
+#pragma unroll
+          for (int q = 0; q < E; ++q) xk.v[q] = ys[(size_t)(k - s) * E + q];  // x~_k = y_k
+          if (tid < E) pr.x[(size_t)k * E + tid] = ys[(size_t)(k - s) * E + tid];
           for (int t = tid; t < 2 * (k - s); t += T) {
             const int j = s + (t >> 1), part = t & 1;
             double* yj = ys + (size_t)(j - s) * E;
@@ -502,8 +574,8 @@ __device__ __forceinline__ void mgs_epilogue(const Params& pr, unsigned& epoch, 
 #pragma unroll
             for (int q = 0; q < L; ++q) yj[part * L + q] = y.v[part * L + q];
           }
+          __syncthreads();
         }
-        __syncthreads();
       }
     }
     if (s == 0) break;
