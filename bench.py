@@ -123,9 +123,9 @@ BATCHED = {
 # complex conjugated multiply-accumulate, complex update y -= c x, |x|^2 accumulate,
 # complex / real division.
 COST = {
-    1: dict(mac=4, upd=4, norm=2, div=2),
-    2: dict(mac=36, upd=42, norm=18, div=22),
-    4: dict(mac=280, upd=322, norm=140, div=608),
+    1: dict(mac=4, upd=4, norm=2, div=3),
+    2: dict(mac=36, upd=42, norm=18, div=23),
+    4: dict(mac=280, upd=322, norm=140, div=409),
 }
 # FP64 peak: 152 SMs x 4 sub-partitions x 0.5 FP64 lanes/clk (one DFMA warp-instruction
 # per 64 cycles per sub-partition, measured) at the 2070 MHz maximum SM clock.
