@@ -50,6 +50,22 @@ def test_c2_dd_256_extreme_vs_oracle(orc):
         assert v <= 10 * n * kap * u, (k, v, kap)
 
 
+@pytest.mark.parametrize("m,n", [(64, 64), (90, 65), (160, 130)])
+def test_qd_extreme_vs_oracle(orc, m, n):
+    """The extreme scaling of the DD workload (rows 10^U{-12..12}, columns 10^U{-4..4}) in
+    quad double, through the QD kernel's paired back substitution (n = 65: a block with an
+    odd row count): x, R and Q against the oracle, err <= 10 n kappa^ u with u = 2^-209."""
+    A, _, b = inputs.system(m, n, 4, 8800 + m + n, extreme=True)
+    g = gpu_ls_solve(A.copy(), b.copy())
+    o = orc.ls_solve(A.copy(), b.copy())
+    assert g["status"] == 0 and o["status"] == 0
+    kap = _kappa(orc, A, o["R"])
+    u = 2.0 ** -209
+    err = dict(x=rel(orc, g["x"], o["x"]), R=rel(orc, upper(g["R"]), upper(o["R"])), Q=rel(orc, g["Q"], o["Q"]))
+    for k, v in err.items():
+        assert v <= 10 * n * kap * u, (k, v, kap)
+
+
 def test_c1_qd_320x256_properties(orc):
     m, n, L = 320, 256, 4
     u = 2.0 ** -209
