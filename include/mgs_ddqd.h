@@ -300,7 +300,8 @@ int mgs_fp64_probe(double* dev_out, int blocks, int threads, int iters, void* st
  *   [0] arrival counter, [1] abort flag, [2] status, [3] the flag of kind 0.
  * After the kernel: [2] = MGS_ETIMEOUT and [1] = 1 once timeout_ns nanoseconds have
  * passed.  A caller that sets [1] = 1 before the call (an abort raised earlier) sees the
- * wait fall through at once, [2] unchanged.  The GPU context stays usable either way.
+ * wait fall through within 64 polls (tens of microseconds), [2] unchanged.  The GPU
+ * context stays usable either way.
  * Stream-ordered, asynchronous.  Host returns: MGS_OK, MGS_EINVAL (null or misaligned
  * words, kind not 0 or 1, timeout_ns outside [1, 1e10]) or MGS_ECUDA.
  */
