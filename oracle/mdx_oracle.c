@@ -22,7 +22,8 @@
  *   - Section 4, Eq. (2): the accuracy measure e = max_ij |a_ij - sum_l q_il r_lj|.
  *
  * Arithmetic.  A real number carries L limbs (L = 1 double, 2 double-double,
- * 4 quad-double); its value is the exact sum of the limbs.  Every elementary operation
+ * 4 quad-double; L = 8 is also accepted, as a reference of twice quad-double precision
+ * for judging a quad-double solve); its value is the exact sum of the limbs.  Every elementary operation
  * (+, -, *) is first evaluated EXACTLY as a floating-point expansion (Shewchuk 1997,
  * "Adaptive precision floating-point arithmetic": error-free two-sum of Knuth, two-product
  * through a fused multiply-add as in Dekker 1971, expansion growth with zero elimination),
@@ -56,7 +57,7 @@
 #define ORACLE_PLANT 0
 #endif
 
-#define LMAX 4
+#define LMAX 8 /* L = 8 (octo-double) serves only as a higher-precision reference */
 #define XCAP 1024 /* capacity of an expansion; long sums compress before reaching it */
 
 typedef struct {
@@ -299,7 +300,7 @@ static mp mp_sqrt(mp s, int L) {
 #if ORACLE_PLANT == 4
   int steps = 0; /* planted: no Newton refinement */
 #else
-  int steps = (L == 1) ? 1 : (L == 2) ? 2 : 3;
+  int steps = (L == 1) ? 1 : (L == 2) ? 2 : (L == 4) ? 3 : 4; /* ceil(log2 L) + 1 */
 #endif
   for (int it = 0; it < steps; ++it) {
     mp r = mp_sub(s, mp_mul(x, x, L), L);
@@ -543,7 +544,7 @@ EXPORT int oracle_backsub(int L, const double *R, int ldr, int n, double *y, dou
  */
 EXPORT int oracle_ls_solve(int L, double *A, double *b, double *x, double *R, double *z, int m, int n, int lda,
                            int ldr) {
-  if (L != 1 && L != 2 && L != 4) return 1;
+  if (L != 1 && L != 2 && L != 4 && L != 8) return 1;
   if (n < 1 || m < n || lda < m) return 1;
   int nc = n + 1;
   size_t es = 2 * (size_t)L;
@@ -576,7 +577,7 @@ EXPORT int oracle_ls_solve(int L, double *A, double *b, double *x, double *R, do
 
 /* QR only (Figure 1 without the augmented column): A (m x n) -> Q in place, R (n x n). */
 EXPORT int oracle_qr(int L, double *A, double *R, int m, int n, int lda, int ldr) {
-  if (L != 1 && L != 2 && L != 4) return 1;
+  if (L != 1 && L != 2 && L != 4 && L != 8) return 1;
   if (n < 1 || m < n || lda < m || ldr < n) return 1;
   return oracle_mgs(L, A, m, n, lda, R, ldr, 0);
 }

@@ -9,17 +9,17 @@ import pins
 from paper_1210_0800_gb300 import inputs
 
 
-@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("L", [2, 4, 8])
 def test_exact_rational(orc, L):
     pins.pin_mgs_exact_rational(orc, L)
 
 
-@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("L", [1, 2, 4, 8])
 def test_special_cases(orc, L):
     pins.pin_mgs_special_cases(orc, L)
 
 
-@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("L", [1, 2, 4, 8])
 def test_backsub(orc, L):
     pins.pin_backsub(orc, L)
 
