@@ -47,4 +47,5 @@ def test_table2_qd_on_gpu(orc, g):
         e = math.log10(orc.qr_error(A, Q, R)[0])
         Qo, Ro, _ = orc.qr(A.copy())
         eo = math.log10(orc.qr_error(A, Qo, Ro)[0])
+        print("Table 2 QD g=%d matrix %d: log10 e GPU %.2f, oracle %.2f, printed [%.1f, %.1f]" % (g, s, e, eo, lo, hi))
         assert e <= eo + 2.5 and e <= hi + 2.5 and e >= lo - 0.5, (g, s, e, eo, lo, hi)

@@ -1,12 +1,15 @@
 """The benchmarked workloads at their full sizes, in the launch configuration the
-benchmark times (the default kernel for each size), checked against the oracle.
+benchmark times (the default plan for each size), checked against the oracle element by
+element: x, R (upper triangle), Q, z and the residual column (Section 3, Figure 1 and
+Eq. 1; Section 6, Figure 3).  The oracle's solves of the large systems run in worker
+processes started at collection (tests/oracle_jobs.py) while the other GPU tests run.
 
-Where the oracle solves the system in seconds (m = n = 32 DD; m = n = 256 DD with
-extreme scaling) the comparison is element by element; for m = 320, n = 256 QD the
-oracle's solve takes minutes, so the result is checked through properties the oracle
-computes exactly at this size: A = QR on sampled columns, Q^H Q = I on sampled columns
-(Section 3), the optimality of x (A^H (b - A x) = 0, Eq. 1) and the residual column.
-The ragged batch is sampled system by system."""
+The extreme-value workloads are judged against a reference that is more exact than any
+solve in the working precision: the same stored numbers solved by the oracle with twice
+the limbs.  Against it, the GPU's error must stay within a fixed factor of the oracle's
+own error in the same precision (Section 4's accuracy rule: what the arithmetic, not the
+scaling, allows; the factor follows the per-operation accuracy of the two arithmetics),
+and below a fixed level that the next lower precision misses."""
 
 import math
 
@@ -19,14 +22,27 @@ from paper_1210_0800_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def _amax(orc, X):
-    return orc.max_abs_diff(X, 0 * X)[0]
-
-
 def _kappa(orc, A, R):
     """kappa^ = ||A||_F ||R^-1||_F, R^-1 from the double-double leading limbs of R."""
     afro = math.sqrt(float(np.sum(A[..., 0] ** 2)))
     return afro * orc.rinv_fro(np.ascontiguousarray(R[..., :2]))
+
+
+def _compare(orc, g, o, b, tol, label):
+    """Element-by-element agreement of a GPU solve g with an oracle solve o."""
+    assert g["status"] == 0 and o["status"] == 0, (label, g["status"], o["status"])
+    bmax = max(orc.max_abs_diff(b, 0 * b)[0], 1e-300)
+    errs = dict(
+        x=rel(orc, g["x"], o["x"]),
+        R=rel(orc, upper(g["R"]), upper(o["R"])),
+        Q=rel(orc, g["Q"], o["Q"]),
+        resid=orc.max_abs_diff(g["resid"], o["resid"])[0] / bmax,
+        z=abs(float(np.sum(g["z"])) - float(np.sum(o["z"]))) / bmax,
+    )
+    print("%s: %s" % (label, {k: "%.2e" % v for k, v in errs.items()}))
+    for k, v in errs.items():
+        assert v <= tol, (label, k, v, tol)
+    return errs
 
 
 def test_c0_dd_32x32_vs_oracle(orc):
@@ -34,76 +50,85 @@ def test_c0_dd_32x32_vs_oracle(orc):
     compare_ls(orc, A, b)
 
 
-def test_c2_dd_256_extreme_vs_oracle(orc):
-    """Rows scaled by 10^U{-12..12}, columns by 10^U{-4..4}: x, R and Q against the
-    oracle relative to kappa^ u (u = 2^-104), with the bound err <= 10 n kappa^ u."""
-    m = n = 256
-    A, _, b = inputs.system(m, n, 2, inputs.system_seed(inputs.workload_seed("c2"), 0), extreme=True)
+@pytest.mark.oracle_jobs("c1_qd_320x256", "dd_256", "dd_512", "qd_512")
+@pytest.mark.parametrize("name", ["c1_qd_320x256", "dd_256", "dd_512", "qd_512"])
+def test_fullsize_vs_oracle(orc, jobs, name):
+    """The headline quad-double m = 320, n = 256 system (the benchmark's first timed
+    system) and the m = n = 256 and 512 sweep points in DD and QD (where the plan picks
+    256 threads per CTA), in the default plan, at 1e-26 (DD) / 1e-56 (QD)."""
+    import oracle_jobs
+
+    A, b = oracle_jobs.inputs_of(name)
+    L = A.shape[-1]
     g = gpu_ls_solve(A.copy(), b.copy())
-    o = orc.ls_solve(A.copy(), b.copy())
-    assert g["status"] == 0 and o["status"] == 0
-    kap = _kappa(orc, A, o["R"])
-    u = 2.0 ** -104
-    err = dict(x=rel(orc, g["x"], o["x"]), R=rel(orc, upper(g["R"]), upper(o["R"])), Q=rel(orc, g["Q"], o["Q"]))
-    print("c2: kappa^ = %.3e, err/(kappa^ u) = %s" % (kap, {k: "%.3g" % (v / (kap * u)) for k, v in err.items()}))
-    for k, v in err.items():
-        assert v <= 10 * n * kap * u, (k, v, kap)
+    o = jobs.get(name)
+    _compare(orc, g, o, b, TOL[L], name)
 
 
+def _errors_vs(orc, got, truth):
+    return dict(x=rel(orc, got["x"], truth["x"]), R=rel(orc, upper(got["R"]), upper(truth["R"])),
+                Q=rel(orc, got["Q"], truth["Q"]))
+
+
+def _judge_extreme(orc, g, ref, truth, low, u, factor, level, label):
+    """g: the GPU solve; ref: the oracle in the same precision; truth: the oracle with
+    twice the limbs; low: the oracle one precision down (leading limbs of the inputs).
+    The GPU must be within `factor` times the oracle's own error plus 100 units u on x, R
+    and Q, and below `level` on x, which the lower precision must miss."""
+    for r in (g, ref, truth, low):
+        assert r["status"] == 0, label
+    eg, eo, el = _errors_vs(orc, g, truth), _errors_vs(orc, ref, truth), _errors_vs(orc, low, truth)
+    print("%s vs truth: gpu %s oracle %s lower precision %s" % (
+        label, {k: "%.2e" % v for k, v in eg.items()}, {k: "%.2e" % v for k, v in eo.items()},
+        {k: "%.2e" % v for k, v in el.items()}))
+    for k in ("x", "R", "Q"):
+        assert eg[k] <= factor * eo[k] + 100 * u, (label, k, eg[k], eo[k])
+    assert eg["x"] <= level < el["x"], (label, eg["x"], level, el["x"])
+    return eg, eo, el
+
+
+@pytest.mark.oracle_jobs("c2_dd", "c2_truth", "c2_d")
+def test_c2_dd_256_extreme_vs_truth(orc, jobs):
+    """Rows scaled by 10^U{-12..12}, columns by 10^U{-4..4} (kappa^ ~ 1e33): the GPU's DD
+    solve against the quad-double solve of the same numbers, next to the DD oracle's and
+    the complex-double solve's errors."""
+    import oracle_jobs
+
+    A, b = oracle_jobs.inputs_of("c2_dd")
+    g = gpu_ls_solve(A.copy(), b.copy())
+    truth, ref, low = jobs.get("c2_truth"), jobs.get("c2_dd"), jobs.get("c2_d")
+    print("c2: kappa^ = %.3e" % _kappa(orc, A, ref["R"]))
+    # the DD kernels' compensated arithmetic is as accurate as the oracle's exactly rounded
+    # DD here (measured: within 2.2x on x, R and Q); x of this system is fixed to ~4e-14 by
+    # its conditioning, while complex double loses it entirely (error ~1)
+    _judge_extreme(orc, g, ref, truth, low, 2.0 ** -104, 10, 1e-8, "c2 DD 256x256 extreme")
+
+
+@pytest.mark.oracle_jobs(*["qdx_%dx%d_L%d" % (m, n, lo) for m, n in ((64, 64), (90, 65), (160, 130))
+                           for lo in (4, 8, 2)])
 @pytest.mark.parametrize("m,n", [(64, 64), (90, 65), (160, 130)])
-def test_qd_extreme_vs_oracle(orc, m, n):
-    """The extreme scaling of the DD workload (rows 10^U{-12..12}, columns 10^U{-4..4}) in
-    quad double, through the QD kernel's paired back substitution (n = 65: a block with an
-    odd row count): x, R and Q against the oracle, err <= 10 n kappa^ u with u = 2^-209."""
-    A, _, b = inputs.system(m, n, 4, 8800 + m + n, extreme=True)
-    g = gpu_ls_solve(A.copy(), b.copy())
-    o = orc.ls_solve(A.copy(), b.copy())
-    assert g["status"] == 0 and o["status"] == 0
-    kap = _kappa(orc, A, o["R"])
-    u = 2.0 ** -209
-    err = dict(x=rel(orc, g["x"], o["x"]), R=rel(orc, upper(g["R"]), upper(o["R"])), Q=rel(orc, g["Q"], o["Q"]))
-    for k, v in err.items():
-        assert v <= 10 * n * kap * u, (k, v, kap)
+def test_qd_extreme_vs_truth(orc, jobs, m, n):
+    """The extreme scaling of the DD workload in quad double, through the QD kernel's
+    paired back substitution (n = 65: a block with an odd row count): the GPU against the
+    oracle's L = 8 solve of the same numbers, next to the QD oracle's and the DD solve's
+    errors."""
+    import oracle_jobs
 
-
-def test_c1_qd_320x256_properties(orc):
-    m, n, L = 320, 256, 4
-    u = 2.0 ** -209
-    A, _, b = inputs.system(m, n, L, inputs.system_seed(inputs.workload_seed("c1"), 0))
+    key = "qdx_%dx%d_L%%d" % (m, n)
+    A, b = oracle_jobs.inputs_of(key % 4)
     g = gpu_ls_solve(A.copy(), b.copy())
-    assert g["status"] == 0
-    Q, R, x = g["Q"], upper(g["R"]), g["x"]
-    # R: real positive diagonal
-    for j in range(n):
-        assert R[j, j, 0, 0] > 0 and not R[j, j, 1].any()
-    kap = _kappa(orc, A, R)
-    amax = _amax(orc, A)
-    # A = QR on sampled columns: backward error O(n u ||A||)
-    for j in (0, 1, n // 2, n - 1):
-        qr_j = orc.matvec(Q, R[j])
-        d, _ = orc.max_abs_diff(qr_j, A[j])
-        assert d <= 10 * n * u * amax, (j, d)
-    # Q^H q_j = e_j on sampled columns: loss of orthogonality O(kappa u)
-    for j in (0, n // 2, n - 1):
-        col = orc.matvec_conjT(Q, Q[j])
-        e = np.zeros_like(col)
-        e[j, 0, 0] = 1.0
-        d, _ = orc.max_abs_diff(col, e)
-        assert d <= 10 * n * kap * u, (j, d, kap)
-    # optimality of x: A^H r = 0 with r = b - A x computed exactly
-    r, _ = orc.residual(A, b, x, Lout=L)
-    ahr = orc.matvec_conjT(A, r)
-    bound = 10 * n * kap * u * (m * amax * amax * _amax(orc, x) + amax * _amax(orc, b))
-    assert _amax(orc, ahr) <= bound, (_amax(orc, ahr), bound)
-    # what MGS leaves of b is the residual b - A x (Eq. 1) and z its norm
-    d, _ = orc.max_abs_diff(g["resid"], r)
-    assert d <= 10 * n * u * (m * amax * _amax(orc, x) + _amax(orc, b)), d
-    rn = math.sqrt(sum(float(np.sum(r[i, :, 0] ** 2)) for i in range(m)))
-    assert abs(float(np.sum(g["z"])) - rn) <= 1e-12 * rn
+    # factor 200: the kernels' quad-double operations (error-free transforms, cascaded
+    # accumulation) are faithful to about one unit of 2^-212, the oracle's exactly rounded
+    # ones to a few hundredths (measured on the host: update y - c x, mean 0.91 against 0.028
+    # units, maximum 24.7 against 0.5), so the solve's error is some 30x the oracle's
+    # (measured 7x to 91x on these systems); the double-double solve misses 1e-40 by 12 or
+    # more decades
+    _judge_extreme(orc, g, jobs.get(key % 4), jobs.get(key % 8), jobs.get(key % 2), 2.0 ** -209, 200, 1e-40,
+                   "QD %dx%d extreme" % (m, n))
 
 
 def test_c1_qd_planted_solution(orc):
-    """b = A x_true at the same size: x recovers x_true to O(n kappa u)."""
+    """b = A x_true at the headline size: x recovers x_true to O(n kappa u)."""
     m, n, L = 320, 256, 4
     A, xt, b = planted_system(m, n, L, inputs.system_seed(inputs.workload_seed("c1"), 1), orc=orc)
     g = gpu_ls_solve(A.copy(), b.copy())
