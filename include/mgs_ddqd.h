@@ -217,14 +217,22 @@ int ls_adjoint_qd_batched(const double* Q_pool, const double* R_pool, const doub
  * ls_solve_dd without a caller workspace, for callers that cannot allocate device memory
  * (a host whose device memory is all owned by another allocator, or an application that
  * must not allocate after start-up).  The paper has no counterpart: it is a packaging of
- * ls_solve_dd.  Arguments and results are those of ls_solve_dd minus the workspace.
- *   Scratch: a fixed device array of MGS_NOALLOC_WORKSPACE_BYTES inside the library,
- *   held by every GPU that loads the library until the process exits.  No allocation
- *   routine is called.
+ * ls_solve_dd.  Arguments and results are those of ls_solve_dd minus the workspace, and
+ * the results are bit for bit those of ls_solve_dd on the same inputs.
+ *   Scratch: a fixed device array of MGS_NOALLOC_WORKSPACE_BYTES inside the library.  With
+ *   lazy module loading (the CUDA default) it is reserved on a device when the first call
+ *   on that device and context loads the library's module, and it stays until the context
+ *   is destroyed (normally at process exit).  No allocation routine is called by this
+ *   entry point; make the first call on each device at start-up, before the host's
+ *   allocator takes the rest of device memory (or set CUDA_MODULE_LOADING=EAGER), else
+ *   that first call can fail with MGS_ECUDA (out of memory).
  *   Sizes whose workspace (mgs_workspace_bytes(2, m, n, 1)) exceeds the array are rejected
- *   with MGS_ENOSPACE (on GB300, m = n <= 346 with the default kernel choice).
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *   with that device current); make it before any stream capture.
+ *   with MGS_ENOSPACE before any work (on GB300, m = n <= 346 fits, 347 does not, with the
+ *   default kernel choice).
+ *   The first call on a device and context looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it for that context; a
+ *   device reset or a new context makes the next call look it up again.  Make the first
+ *   call before any stream capture.
  *   Every call shares the array: calls that may overlap on the GPU race and must not be
  *   issued.  Each call clears what must start at zero itself.
  */
@@ -280,6 +288,11 @@ int newton_step_dd(double* J, int ldj, double* F, double* x, int m, int n, doubl
                    void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 int newton_step_qd(double* J, int ldj, double* F, double* x, int m, int n, double tol, mgs_newton_state* dev_state,
                    void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+/* ======================================================================================
+ * Diagnostics.  Not part of the solve: a measurement hook (the FP64 rate the roofline is
+ * quoted against) and a failure-detection hook (a bounded wait run out on purpose).
+ * ====================================================================================== */
 
 /*
  * FP64 throughput probe (no counterpart in the paper): launches `blocks` x `threads`
