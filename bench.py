@@ -6,8 +6,8 @@ the GPU, through the C ABI; the systems are distinct, pre-generated and resident
 (5.3 MB each) are all distinct, so every step reads data that is not in L2 from the step
 before (total far above the 129 MB L2).
 
-Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead (a bounded
-sample of the same workload, scaled by the algorithmic work).  Multi-GPU: replicas only
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead: every step
+solves in full the system the GPU arm times at that step, one process per host core.  Multi-GPU: replicas only
 (the solves of a path are sequential; independent systems shard with no collective).
 """
 
@@ -133,8 +133,9 @@ SMS, FP64_LANES_PER_CLK_SM = 152, 2.0
 
 
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
-L2_NOTE = ("every step reads its own distinct inputs, untouched since a %d MB write flushed L2 after "
-           "setup and warm-up (only the workspace is reused across steps)" % (L2_FLUSH_BYTES >> 20))
+L2_NOTE = ("every step solves its own distinct system(s), with inputs no earlier step touched (GPU arm: a %d MB "
+           "write flushed L2 after setup and warm-up; only the workspace is reused across steps)"
+           % (L2_FLUSH_BYTES >> 20))
 
 
 def flush_l2(dev):
@@ -261,54 +262,158 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(L, m, n, seconds_target=3.0):
-    """Time the CPU oracle on a bounded sample of the workload: one system with the same m
-    and limbs and fewer columns, chosen so one solve takes a few seconds; returns
-    (systems/s scaled to the full workload by the algorithmic work, description)."""
+def shared_config(workload: str, world: int, **extra) -> dict:
+    """The workload's config, identical in both arms (the oracle arm solves the same
+    systems as the GPU's timed steps)."""
+    cfg = {"workload": workload}
+    cfg.update(extra)
+    cfg["l2"] = L2_NOTE
+    cfg["parallelism"] = ("replicas: one independent system per step on every GPU" if world > 1
+                          else "one independent system per step")
+    return cfg
+
+
+def single_config(workload: str, world: int) -> dict:
+    L, m, n, extreme = WORKLOADS[workload]
+    return shared_config(workload, world, limbs=L, m=m, n=n, extreme=extreme, systems_per_step=1)
+
+
+def batched_config(workload: str, world: int) -> dict:
+    L, batch, n_rng, e_rng = BATCHED[workload]
+    return shared_config(workload, world, limbs=L, systems_per_step=batch, n_range=list(n_rng),
+                         m_minus_n_range=list(e_rng))
+
+
+def diff_config(workload: str, world: int) -> dict:
+    L, m, n, B = DIFF[workload]
+    return shared_config(workload, world, limbs=L, m=m, n=n, systems_per_step=B,
+                         step="forward solve + adjoint (dL/dA, dL/db for L = sum |x|^2)")
+
+
+def newton_config(workload: str, world: int) -> dict:
+    L, m, n, S = NEWTON[workload]
+    return shared_config(workload, world, limbs=L, m=m, n=n, newton_steps_per_run=S)
+
+
+def workload_config(workload: str, world: int):
+    """(config, unit) of a workload, shared by both arms."""
+    if workload in WORKLOADS:
+        return single_config(workload, world), "systems/s"
+    if workload in BATCHED:
+        return batched_config(workload, world), "systems/s"
+    if workload in DIFF:
+        return diff_config(workload, world), "systems/s"
+    return newton_config(workload, world), "Newton steps/s (one solve each)"
+
+
+def cmacs(L: int, m: int, n: int) -> float:
+    """Complex multiply-accumulates of the projections and updates of one solve (the
+    paper's operation count: m n (n + 1), half projections r_kj = q_k^H a_j, half updates
+    a_j -= r_kj q_k over the augmented [A b]); independent of how a primitive is built."""
+    return float(m) * n * (n + 1)
+
+
+def _ref_problem(workload: str, index: int):
+    """(kind, limbs, A, b) of the system the GPU arm times as step `index` (rank 0)."""
+    if workload in WORKLOADS:
+        L, m, n, extreme = WORKLOADS[workload]
+        A, _, b = inputs.system(m, n, L, replica_seed(workload, 0, index), extreme=extreme)
+        return "solve", L, A, b
+    if workload in BATCHED:
+        L, batch, n_rng, e_rng = BATCHED[workload]
+        seed = inputs.system_seed(inputs.BASE_SEED + 3, 0)
+        ms, ns = inputs.ragged_shapes(batch, seed, n_rng[0], n_rng[1], e_rng[0], e_rng[1])
+        i = index % batch
+        A, _, b = inputs.system(int(ms[i]), int(ns[i]), L, inputs.system_seed(seed, i))
+        return "solve", L, A, b
+    if workload in DIFF:
+        L, m, n, B = DIFF[workload]
+        A, _, b = inputs.system(m, n, L, replica_seed(workload, 0, index % B))
+        return "adjoint", L, A, b
+    L, m, n, S = NEWTON[workload]
+    A, x0, b = inputs.system(m, n, L, replica_seed(workload, 0, index % S))
+    return "newton", L, A, (b, x0)
+
+
+def _ref_task(task):
+    """One oracle step (a worker-process entry point): returns (seconds, status, what)."""
+    workload, index = task
     import oracle
 
     o = oracle.get()
-    # calibrate on a tiny system, then size the sample
-    ns = 8
-    A, xt, b = inputs.system(m, ns, L, inputs.BASE_SEED + 99)
+    kind, L, A, b = _ref_problem(workload, index)
     t0 = time.perf_counter()
-    o.ls_solve(A, b)
-    t_small = time.perf_counter() - t0
-    scale = lambda k: m * (k + 1) ** 2  # noqa: E731  (work of MGS on [A b])
-    ns2 = int(max(ns, min(n, (ns + 1) * math.sqrt(seconds_target / max(t_small, 1e-6) * 1.0) - 1)))
-    A, xt, b = inputs.system(m, ns2, L, inputs.BASE_SEED + 98)
-    t0 = time.perf_counter()
-    o.ls_solve(A, b)
+    if kind == "solve":
+        st = o.ls_solve(A, b)["status"]
+    elif kind == "adjoint":
+        r = o.ls_solve(A.copy(), b.copy())
+        st = max(r["status"], o.ls_adjoint(A, b, 2.0 * r["x"])[3])
+    else:
+        st = o.newton_step(A, b[0], b[1])[3]
     dt = time.perf_counter() - t0
-    sys_per_s = (1.0 / dt) * (fp64_ops(L, m, ns2) / fp64_ops(L, m, n))
-    desc = ("oracle ls_solve of one %s system m=%d n=%d (sample of the m=%d n=%d workload), %.2f s, scaled by "
-            "the algorithmic FP64-operation ratio %.4f" % ("QD" if L == 4 else "DD", m, ns2, m, n, dt,
-                                                          fp64_ops(L, m, ns2) / fp64_ops(L, m, n)))
-    del scale
-    return sys_per_s, desc, dt
+    return dt, st, "%s of a complex %s %dx%d system" % ({"solve": "ls_solve", "adjoint": "ls_solve + ls_adjoint",
+                                                         "newton": "newton_step"}[kind],
+                                                        {1: "D", 2: "DD", 4: "QD"}[L], A.shape[1], A.shape[0])
 
 
-def run_reference(args, L, m, n, rank, world):
+def _ref_warm(_):
+    import oracle
+
+    o = oracle.get()
+    A, _, b = inputs.system(8, 8, 2, 1)
+    o.ls_solve(A, b)
+    return os.getpid()
+
+
+def cpu_baseline(workload: str, count: int, first: int):
+    """The oracle on this host, one core: `count` steps of the workload (the systems the
+    GPU timed from index `first` on), each solved in full; returns the cpu_baseline entry
+    (steps per second)."""
+    total, what = 0.0, ""
+    for i in range(count):
+        dt, _, what = _ref_task((workload, first + i))
+        total += dt
+    return {"value": count / total, "unit": "systems/s" if workload not in NEWTON else "Newton steps/s",
+            "cores": 1, "kind": "oracle",
+            "sample": "%d full step%s on one core, each an oracle %s that the GPU arm also solves; %.1f s" % (
+                count, "s" if count > 1 else "", what, total)}
+
+
+def run_reference(args, config, unit, rank, world):
+    """The oracle arm: every one of the K steps solves in full the system the GPU arm
+    times at that step, one step per process, min(K, host cores) processes at a time;
+    value = K / wall-clock seconds of the timed region."""
     if rank != 0:
         return 0
-    vals, descs = [], []
-    for _ in range(args.warmup):
-        oracle_sample(L, m, n, args.ref_seconds)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, d, _ = oracle_sample(L, m, n, args.ref_seconds)
-        vals.append(v)
-        descs.append(d)
-    wall = time.perf_counter() - t0
-    value = statistics.median(vals)
+    import multiprocessing as mproc
+
+    K, W = args.steps, args.warmup
+    cores = os.cpu_count() or 1
+    procs = max(1, min(K, cores))
+    ctx = mproc.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_ref_warm, range(procs))  # workers up and the oracle loaded in each
+        for i in range(W):  # warm-up steps: small systems, untimed
+            pool.map(_ref_warm, range(procs))
+        t0 = time.perf_counter()
+        res = pool.map(_ref_task, [(args.workload, W + i) for i in range(K)], chunksize=1)
+        wall = time.perf_counter() - t0
+    secs = [r[0] for r in res]
+    bad = sum(1 for r in res if r[1] != 0)
+    value = K / wall
+    desc = ("%d full steps, each the %s the GPU arm times at that step; %d processes on %d host cores; "
+            "median %.3g s per step on one core" % (K, res[0][2], procs, cores, statistics.median(secs)))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1000.0 * wall / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "parallelism": "single CPU core"},
-        "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": descs[-1]},
-        "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": procs, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "single_core_s_per_step": statistics.median(secs),
+        "nproc": cores,
         "wall_s": wall,
+        "status_errors": bad,
     }
     print(json.dumps(line))
     return 0
@@ -410,9 +515,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
         "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "extreme": extreme,
-                   "systems_per_step": 1, "l2": L2_NOTE,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": single_config(args.workload, world),
         "e2e": {"value": world / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": K,
@@ -423,6 +526,10 @@ def run_gpu(args, L, m, n, extreme, rank, world):
                              "(%.4g) / CUDA-event time per solve; each instruction counted as one FMA slot "
                              "(2 flops) like the peak (152 SMs x 2 DFMA/clk x %.0f MHz)" % (ops, sm_max)},
         "kernel_ms": kernel_ms,
+        "cmac_rate": {"value": cmacs(L, m, n) / (kernel_ms / 1000.0) / 1e9, "unit": "G complex MAC/s",
+                      "per_solve": cmacs(L, m, n),
+                      "note": "m n (n + 1) complex multiply-accumulates of the projections and updates per "
+                              "solve / CUDA-event time per solve; independent of the primitives' cost"},
         "hbm": {"bytes_per_solve": hbm_bytes(L, m, n), "achieved_gbs": hbm_bytes(L, m, n) / kernel_ms / 1e6,
                 "note": "algorithmic bytes / kernel time; the solve is FP64-bound, not HBM-bound"},
         "status_errors": len(bad),
@@ -434,8 +541,7 @@ def run_gpu(args, L, m, n, extreme, rank, world):
     line["roofline"]["measured_fp64_fma_per_s"] = probe
     line["roofline"]["measured_over_derived_peak"] = probe / peak_ops
     if world == 1 and not args.no_cpu_baseline:
-        v, desc, dt = oracle_sample(L, m, n, args.ref_seconds * 6)  # about 12 s of CPU work
-        line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(args.workload, 1, W)
     print(json.dumps(line))
     return 0
 
@@ -544,12 +650,10 @@ def run_gpu_batched(args, rank, world):
         "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "limbs": L, "systems_per_step": batch, "n_range": list(n_rng),
-                   "m_minus_n_range": list(e_rng), "max_m": base.max_m, "max_n": base.max_n,
-                   "launch": "one persistent launch per step, replayed from a CUDA graph",
-                   "tune": {"threads": best[0], "ctas_per_sm": best[1], "candidates_ms": times},
-                   "l2": L2_NOTE,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": batched_config(args.workload, world),
+        "launch": {"max_m": base.max_m, "max_n": base.max_n,
+                   "how": "one persistent launch per step, replayed from a CUDA graph",
+                   "tune": {"threads": best[0], "ctas_per_sm": best[1], "candidates_ms": times}},
         "e2e": {"value": world * batch / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": base.x_pool.numel() * 8},
         "gpu_launches": K,
@@ -558,6 +662,8 @@ def run_gpu_batched(args, rank, world):
                      "note": "FP64 pipe: algorithmic FP64 instructions of all systems (%.4g) per launch / "
                              "CUDA-event time per launch" % ops},
         "kernel_ms": kernel_ms,
+        "cmac_rate": {"value": sum(cmacs(L, A.shape[1], A.shape[0]) for A, _ in host) / (kernel_ms / 1000.0) / 1e9,
+                      "unit": "G complex MAC/s"},
         "sequential_plain": {"value": len(sel) / (seq_ms / 1000.0), "unit": "systems/s",
                              "systems": len(sel), "frac": (seq_ops / (seq_ms / 1000.0)) / peak_ops,
                              "note": "the same systems (every %d-th) solved one after another with the "
@@ -567,18 +673,7 @@ def run_gpu_batched(args, rank, world):
     if clk:
         line["clocks"] = clk
     if world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        o = oracle.get()
-        small = sorted(range(batch), key=lambda i: host[i][0].shape[0])[:8]
-        t0 = time.perf_counter()
-        for i in small:
-            o.ls_solve(host[i][0].copy(), host[i][1].copy())
-        dt = time.perf_counter() - t0
-        frac_work = sum(fp64_ops(L, host[i][0].shape[1], host[i][0].shape[0]) for i in small) / ops
-        line["cpu_baseline"] = {"value": batch * frac_work / dt, "unit": "systems/s", "cores": 1, "kind": "oracle",
-                                "sample": "oracle ls_solve of the 8 smallest systems of the batch (%.2f s), scaled "
-                                          "by their share %.5f of the batch's FP64 operations" % (dt, frac_work)}
+        line["cpu_baseline"] = cpu_baseline(args.workload, 8, 0)
     print(json.dumps(line))
     return 0
 
@@ -696,10 +791,9 @@ def run_gpu_newton(args, rank, world):
         "metric": METRIC, "value": world * S / (ms / 1000.0), "unit": "Newton steps/s (one solve each)",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "newton_steps_per_run": S,
-                   "step": "one CUDA-graph replay of %d gated newton_step calls, J and F copied in from device "
-                           "memory before each" % S, "l2": L2_NOTE,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": newton_config(args.workload, world),
+        "step": "one CUDA-graph replay of %d gated newton_step calls, J and F copied in from device memory "
+                "before each" % S,
         "e2e": {"value": world * S / (e2e_ms / 1000.0), "unit": "Newton steps/s",
                 "h2d_bytes_per_step": x0h.numel() * 8, "d2h_bytes_per_step": xh.numel() * 8 + sh.numel()},
         "gpu_launches": 3 * S * K,
@@ -802,10 +896,8 @@ def run_gpu_diff(args, rank, world):
         "metric": METRIC, "value": world * B / (ms / 1000.0), "unit": "systems/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "limbs": L, "m": m, "n": n, "systems_per_step": B,
-                   "step": "forward solve + adjoint (dL/dA, dL/db for L = sum |x|^2) via torch.autograd.Function",
-                   "l2": L2_NOTE,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": diff_config(args.workload, world),
+        "through": "torch.autograd.Function (the forward solve and the hand-written adjoint kernel)",
         "e2e": {"value": world * B / (e2e_ms / 1000.0), "unit": "systems/s",
                 "h2d_bytes_per_step": Ah.numel() * 8 + bh.numel() * 8,
                 "d2h_bytes_per_step": gAh.numel() * 8 + gbh.numel() * 8},
@@ -831,7 +923,6 @@ def main(argv=None):
     ap.add_argument("--workload", default=DEFAULT,
                     choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(DIFF) + sorted(NEWTON))
     ap.add_argument("--seq-sample", type=int, default=64, help="systems solved one by one for the comparison")
-    ap.add_argument("--ref-seconds", type=float, default=2.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="one line per point of the m = n in {64, 128, 256, 512} DD and QD sweep")
@@ -846,22 +937,16 @@ def main(argv=None):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    if args.impl == "reference":
+        config, unit = workload_config(args.workload, world)
+        return run_reference(args, config, unit, rank, world)
     if args.workload in NEWTON:
-        if args.impl == "reference":
-            L, m, n, S = NEWTON[args.workload]
-            return run_reference(args, L, m, n, rank, world)
         return run_gpu_newton(args, rank, world)
     if args.workload in DIFF:
-        if args.impl == "reference":
-            L, m, n, B = DIFF[args.workload]
-            return run_reference(args, L, m, n, rank, world)
         return run_gpu_diff(args, rank, world)
     if args.workload in BATCHED:
-        if args.impl == "reference":
-            L, batch, n_rng, e_rng = BATCHED[args.workload]
-            return run_reference(args, L, (n_rng[0] + n_rng[1]) // 2 + 8, (n_rng[0] + n_rng[1]) // 2, rank, world)
         return run_gpu_batched(args, rank, world)
-    if args.sweep and args.impl == "ours":
+    if args.sweep:
         args.no_cpu_baseline = True
         for wl in SWEEP:
             args.workload = wl
@@ -871,8 +956,6 @@ def main(argv=None):
                 return rc
         return 0
     L, m, n, extreme = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        return run_reference(args, L, m, n, rank, world)
     return run_gpu(args, L, m, n, extreme, rank, world)
 
 

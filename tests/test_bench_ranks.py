@@ -33,8 +33,9 @@ def _worker(rank, world, port, out):
     gathered = [None] * world
     dist.all_gather_object(gathered, seeds)
     # the reference arm: ranks other than 0 return at once, without work or output
-    rc = bench.run_reference(type("A", (), {"steps": 1, "warmup": 0, "ref_seconds": 0.01, "gpus": world,
-                                            "workload": "c1_qd_320x256"})(), 4, 320, 256, rank, world) \
+    cfg, unit = bench.workload_config("c1_qd_320x256", world)
+    rc = bench.run_reference(type("A", (), {"steps": 1, "warmup": 0, "gpus": world,
+                                            "workload": "c1_qd_320x256"})(), cfg, unit, rank, world) \
         if rank != 0 else 0
     dist.destroy_process_group()
     out[rank] = (got, gathered, rc)
