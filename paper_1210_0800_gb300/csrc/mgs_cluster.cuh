@@ -4,17 +4,21 @@
 // release/acquire flags.  Same method, tiles and arithmetic as mgs_ls_kernel (Section 3,
 // Figure 1 and Eq. 1; Section 6, Figure 3).
 //
-// Step k in the cluster that owns column k+1 (the critical path):
-//   A: partials of G_kk = ||a_k||^2 and G_{k,k+1} over its rows -> cluster reduction ->
-//      c_{k,k+1} = G_{k,k+1} / G_kk -> update column k+1 -> publish its rows;
-// then, in every cluster,
-//   B: partials of its other trailing columns (and of G_kk where A did not run) -> cluster
-//      reduction -> coefficients -> update -> (wait for the rows of pivot k+1).
+// The pivot hand-off chain (the critical path): the cluster that owns column k+1 turns it
+// into pivot k+1 in step k (A: partials of G_kk = ||a_k||^2 and G_{k,k+1} over its rows ->
+// cluster reduction -> c_{k,k+1} = G_{k,k+1} / G_kk -> update column k+1 -> publish its
+// rows).  Two-step look-ahead: the cluster that owns column k+2 applies pivot k to that
+// column first (the same phase without the publication), then waits for pivot k+1 and runs
+// A(k+1) at once, and only then does its bulk work of steps k and k+1.  So no cluster does
+// bulk work between receiving the pivot before its own and publishing its own, and the
+// chain advances at the speed of A plus the hand-off, not of the bulk.
+//   Bulk (B) of step k in every cluster: partials of its other trailing columns (and of
+//   G_kk where no critical phase formed it) -> cluster reduction -> coefficients ->
+//   update -> (wait for the rows of pivot k+1).
 // Every cluster forms G_kk from the pivot rows it holds, so nothing but the pivot itself
-// passes between clusters: the owner of the next pivot hands it on before its own bulk
-// work and the other clusters' bulk work overlaps the hand-off chain.  The clusters sum
-// G_kk's terms in different orders; the owner of column k+1 stores its value, which gives
-// r_kk.  One grid barrier before the normalisation epilogue.
+// passes between clusters.  The clusters sum G_kk's terms in different orders; the owner of
+// column k+1 stores its value, which gives r_kk.  One grid barrier before the
+// normalisation epilogue.
 //
 // HW = true: the Br CTAs form a hardware cluster (cluster.sync, partials read through
 // distributed shared memory); clusters must fit in a GPC, which can leave SMs idle.
@@ -57,17 +61,20 @@ __device__ __forceinline__ void group_barrier(const Params& pr, unsigned* ctr, u
   __syncthreads();
 }
 
-// Doubles of global partials the HW = false variant needs (two B buffers and one A buffer
-// per CTA, `wmax` = columns of the widest group).
+// Doubles of global partials the HW = false variant needs (two B buffers and two A
+// buffers per CTA, `wmax` = columns of the widest group).
 __host__ __device__ inline size_t group_partials_doubles(int L, int Br, int Bc, int wmax) {
-  return (size_t)Bc * Br * (2 * (size_t)(wmax + 1) * 2 * L + (size_t)2 * 2 * L);
+  return (size_t)Bc * Br * (2 * (size_t)(wmax + 1) * 2 * L + (size_t)2 * 2 * 2 * L);
 }
 
-// Extra shared memory of the cluster kernel on top of smem_bytes(): B partials (two
-// buffers of w + 1 items x 2 parts), A partials (2 items x 2 parts), reduced values.
+// Shared memory of the cluster kernel: the tile and three pivot buffers (pivots k, k+1
+// and k+2 are live at once in the look-ahead), coefficients, scalars, the reduction tree,
+// B partials (two buffers of w + 1 items x 2 parts), A partials (two buffers of 2 items x
+// 2 parts), reduced values.
 __host__ __device__ inline size_t cluster_smem_bytes(int L, int h, int w, int T) {
-  return smem_bytes(L, h, w, T) +
-         sizeof(double) * (2 * (size_t)(w + 1) * 2 * L + (size_t)2 * 2 * L + (size_t)(w + 2) * 2 * L) + 64;
+  return smem_bytes(L, h, w, T) + sizeof(double) * ((size_t)2 * L * h + 2 * (size_t)(w + 1) * 2 * L +
+                                                    (size_t)2 * 2 * 2 * L + (size_t)(w + 2) * 2 * L) +
+         64;
 }
 
 template <class Ar, bool HW, int T>
@@ -88,10 +95,12 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
   const int r0 = p * h;
   const int hr = max(0, min(h, pr.m - r0));
   const int w = (nc - c + Bc - 1) / Bc;
-  // published pivot rows live in a ring of Bc + 2 slots: a cluster that still has to read
-  // pivot j owns a column below j + Bc, and no pivot beyond that column is published before
-  // it has read (the pivots follow one release/acquire chain), so slot j is free again
-  // when pivot j + Bc + 2 is written
+  // published pivot rows live in a ring of Bc + 2 slots.  A cluster loads every pivot below
+  // a column before it publishes that column (it takes the steps in order, and the
+  // look-ahead only moves its bulk work later); every cluster that still has work after
+  // step j owns one of the columns j + 1 .. j + Bc; and pivots are published in order (each
+  // owner waits for the previous pivot).  So by the time pivot j + Bc + 1 or later is
+  // written, every cluster that needs pivot j has loaded it, and slot j is free again.
   const int vslots = Bc + 2;
   unsigned epoch = 0, gepoch = 0;
   unsigned* gctr = pr.gsync + (size_t)c * 32;  // this group's arrival counter (HW = false)
@@ -104,18 +113,18 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
 
   extern __shared__ __align__(16) double sm[];
   double* tile = sm;                         // w * E * h
-  double* piv = tile + (size_t)w * E * h;    // 2 * E * h
-  double* coef = piv + (size_t)2 * E * h;    // w * E
+  double* piv = tile + (size_t)w * E * h;    // 3 * E * h: pivot k in buffer k % 3
+  double* coef = piv + (size_t)3 * E * h;    // w * E
   double* gkk = coef + (size_t)w * E;        // E
   double* scal = gkk + E;                    // 4 * E
   double* redb = scal + 4 * E;               // T * L
   double* pbuf = redb + (size_t)T * L;        // 2 x (w + 1) x 2 x PACC
-  double* pabuf = pbuf + 2 * (size_t)(w + 1) * 2 * PACC;  // 2 x 2 x PACC
-  double* gres = pabuf + 2 * 2 * PACC;               // (w + 2) x E reduced values
+  double* pabuf = pbuf + 2 * (size_t)(w + 1) * 2 * PACC;  // 2 x 2 x 2 x PACC
+  double* gres = pabuf + 2 * 2 * 2 * PACC;           // (w + 2) x E reduced values
   // HW = false: the partial buffers live in global memory, CTA-major within a group so
   // that peer pp's buffer is `stride` doubles from ours
   const int wmax = (nc + Bc - 1) / Bc;
-  const size_t gstride = 2 * (size_t)(wmax + 1) * 2 * PACC + (size_t)2 * 2 * PACC;
+  const size_t gstride = 2 * (size_t)(wmax + 1) * 2 * PACC + (size_t)2 * 2 * 2 * PACC;
   if constexpr (!HW) {
     pbuf = pr.P + ((size_t)c * Br + p) * gstride;
     pabuf = pbuf + 2 * (size_t)(wmax + 1) * 2 * PACC;
@@ -123,6 +132,9 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
   const int pbw = HW ? w : wmax;  // B-buffer width in items - 1
   int* iflag = reinterpret_cast<int*>(gres + (size_t)(w + 2) * E);
   pacc* red = reinterpret_cast<pacc*>(redb);
+  (void)scal;
+  (void)gkk;
+  auto pbk = [&](int k) { return piv + (size_t)(k % 3) * E * h; };  // pivot k's rows
 
   auto col_of = [&](int s) { return c + s * Bc; };
   auto colptr = [&](int j, int i) -> double* {
@@ -270,96 +282,86 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     }
   };
 
-  // ---------------------------------------------------------------- the steps
-  for (int k = 0; k < nc; ++k) {
-    const int cur = k & 1, nxt = cur ^ 1;
-    const double* pcur = piv + (size_t)cur * E * h;
-    double* pnxt = piv + (size_t)nxt * E * h;
-    const bool last = (k == nc - 1);
-    const bool own_k = (k % Bc) == c;
-    const bool own_k1 = !last && ((k + 1) % Bc) == c;
-    const int s1 = (k + 1) / Bc;
-    const int s0 = (k + 1 - c + Bc - 1) / Bc;
-    const int first = max(s0, 0);
-    const int nact = w - first;  // own columns j > k
-    if (nact <= 0 && !(last && own_k)) break;  // nothing left for this cluster
-    MGS_TR(k, 0);
+  unsigned bph = 0;  // B reductions so far (selects the B-partials buffer)
 
-    real G{};
-    // ---------------------------------------------------------------- A: the critical column
-    if (own_k1) {
-      item_partials(pcur, 2, [&](int it) { return it == 0 ? -1 : s1; }, pabuf);
-      group_sync();
-      cluster_reduce(pabuf, 2, [](int it) { return it == 0; });
-      G = Ar::re(sm_load<Ar>(gres, 1, 0));
-      const bool ok = Ar::positive(G);
-      if (p == 0 && tid == 0) {
-        st_real(pr.Gd + (size_t)k * L, G);
-        if (!ok) set_status(pr.status, ST_ERANK);
-      }
-      coef_of(s1, G, ok, gres + E);
-      __syncthreads();
-      double* ts = tile + (size_t)s1 * E * h;
-      elem cc;
+  // Critical phase: pivot kk (rows at pbk(kk)) applied to the owned column j alone --
+  // partials of G_kk and G_{kk,j} over this CTA's rows, cluster reduction, c_{kk,j},
+  // update of column j (row kk of R stored).  With `publish` (j = kk + 1) the updated
+  // rows are pivot kk + 1: copied to pbk(kk + 1), published in the ring with this row
+  // block's flag, and G_kk is recorded.  Returns G_kk.  `ab` selects the A-partials buffer
+  // (the pre-phase and the phase that follows it use different ones).
+  auto critical = [&](int kk, int j, bool publish, int ab) -> real {
+    const double* pc = pbk(kk);
+    const int sj = (j - c) / Bc;
+    double* pa = pabuf + (size_t)ab * 2 * 2 * PACC;
+    item_partials(pc, 2, [&](int it) { return it == 0 ? -1 : sj; }, pa);
+    group_sync();
+    cluster_reduce(pa, 2, [](int it) { return it == 0; });
+    const real G = Ar::re(sm_load<Ar>(gres, 1, 0));
+    const bool ok = Ar::positive(G);
+    if (publish && p == 0 && tid == 0) {
+      st_real(pr.Gd + (size_t)kk * L, G);
+      if (!ok) set_status(pr.status, ST_ERANK);
+    }
+    coef_of(sj, G, ok, gres + E);
+    __syncthreads();
+    double* ts = tile + (size_t)sj * E * h;
+    elem cc;
 #pragma unroll
-      for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s1 * E + q];
-      for (int t = tid; t < 2 * hr; t += T) {
-        const int l = t >> 1, part = t & 1;
-        elem y = sm_load_part<Ar>(ts, h, l, part);
-        Ar::update_part(f, y, cc, sm_load<Ar>(pcur, h, l), part);
+    for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)sj * E + q];
+    if (p == 0 && tid == 0) g_store<Ar>(j < pr.n ? pr.R + ((size_t)j * pr.ldr + kk) * E : pr.Y + (size_t)kk * E, cc);
+    double* pn = publish ? pbk(kk + 1) : nullptr;
+    for (int t = tid; t < 2 * hr; t += T) {
+      const int l = t >> 1, part = t & 1;
+      elem y = sm_load_part<Ar>(ts, h, l, part);
+      Ar::update_part(f, y, cc, sm_load<Ar>(pc, h, l), part);
 #pragma unroll
-        for (int q = 0; q < L; ++q) {
-          ts[(part * L + q) * h + l] = y.v[part * L + q];
-          pnxt[(part * L + q) * h + l] = y.v[part * L + q];
-        }
+      for (int q = 0; q < L; ++q) {
+        ts[(part * L + q) * h + l] = y.v[part * L + q];
+        if (publish) pn[(part * L + q) * h + l] = y.v[part * L + q];
       }
+    }
+    if (publish) {
       for (int l = hr + tid; l < h; l += T) {
 #pragma unroll
-        for (int q = 0; q < E; ++q) pnxt[q * h + l] = 0.0;
+        for (int q = 0; q < E; ++q) pn[q * h + l] = 0.0;
       }
       __syncthreads();
-      double* vdst = pr.V + ((size_t)((k + 1) % vslots) * Br + p) * h * E;
-      for (int l = tid; l < h; l += T) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pnxt, h, l));
+      double* vdst = pr.V + ((size_t)((kk + 1) % vslots) * Br + p) * h * E;
+      for (int l = tid; l < h; l += T) g_store<Ar>(vdst + (size_t)l * E, sm_load<Ar>(pn, h, l));
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        st_release_s32(pr.flags + (size_t)(k + 1) * Br + p, 1);
+        st_release_s32(pr.flags + (size_t)(kk + 1) * Br + p, 1);
       }
+    } else {
+      __syncthreads();
     }
-    MGS_TR(k, 1);
+    return G;
+  };
 
-    // ---------------------------------------------------------------- B: the other columns
-    // items: the pivot's norm unless A formed it, then the trailing columns other than
-    // k+1 when A updated that one
-    const bool norm_here = !own_k1;
-    const int sb = own_k1 ? first + 1 : first;
+  // Bulk phase of step kk on the owned slots [sb, w): partials (with G_kk's unless
+  // `haveG`), cluster reduction, coefficients, R/y stores, updates.  Returns G_kk.
+  auto bulk = [&](int kk, int sb, bool haveG, real G) -> real {
+    const double* pc = pbk(kk);
+    const bool norm_here = !haveG;
     const int nb = w - sb;
     const int nitB = nb + (norm_here ? 1 : 0);
-    double* pb = pbuf + (size_t)cur * (pbw + 1) * 2 * PACC;
     if (nitB > 0) {
+      // the two buffers alternate between consecutive reductions: a peer reads one while
+      // this CTA may already write the other, and a buffer is written again only after
+      // the next reduction's cluster barrier
+      double* pb = pbuf + (size_t)(bph & 1u) * (pbw + 1) * 2 * PACC;
+      ++bph;
       auto slotB = [&](int it) { return norm_here ? (it == 0 ? -1 : sb + it - 1) : sb + it; };
-      item_partials(pcur, nitB, slotB, pb);
-      MGS_TR(k, 6);
+      item_partials(pc, nitB, slotB, pb);
+      MGS_TR(kk, 6);
       group_sync();
       cluster_reduce(pb, nitB, [&](int it) { return norm_here && it == 0; });
     }
-    MGS_TR(k, 2);
-    if (norm_here) {
-      G = Ar::re(sm_load<Ar>(gres, 1, 0));
-    }
-    if (last) {
-      // only the owner of the last column is left; for [A b] its norm is z and what is
-      // left of it is the residual b - A x
-      if (p == 0 && tid == 0) {
-        st_real(pr.Gd + (size_t)k * L, G);
-        if (!pr.aug && !Ar::positive(G)) set_status(pr.status, ST_ERANK);
-      }
-      if (pr.aug) {
-        const double* ts = tile + (size_t)(k / Bc) * E * h;
-        for (int l = tid; l < hr; l += T) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
-        break;
-      }
-    }
+    MGS_TR(kk, 2);
+    if (norm_here) G = Ar::re(sm_load<Ar>(gres, 1, 0));
+    if (nb <= 0) return G;
     const bool okpiv = Ar::positive(G);
     {
       const double invG = Ar::inv_lead(G);
@@ -379,33 +381,83 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
       }
     }
     __syncthreads();
-    MGS_TR(k, 3);
-    // coefficients of row k to R (row k) and Y (column b); scaled by r_kk at the end
+    MGS_TR(kk, 3);
+    // coefficients of row kk to R (row kk) and Y (column b); scaled by r_kk at the end
     if (p == 0) {
-      for (int t = tid; t < nact; t += T) {
-        const int s = first + t, j = col_of(s);
+      for (int t = tid; t < nb; t += T) {
+        const int s = sb + t, j = col_of(s);
         elem cc;
 #pragma unroll
         for (int q = 0; q < E; ++q) cc.v[q] = coef[(size_t)s * E + q];
         if (j < pr.n)
-          g_store<Ar>(pr.R + ((size_t)j * pr.ldr + k) * E, cc);
+          g_store<Ar>(pr.R + ((size_t)j * pr.ldr + kk) * E, cc);
         else
-          g_store<Ar>(pr.Y + (size_t)k * E, cc);
+          g_store<Ar>(pr.Y + (size_t)kk * E, cc);
       }
     }
-    // update the columns of B
-    update_slots<Ar, T>(f, tile, coef, pcur, h, hr, sb, nb);
-    MGS_TR(k, 4);
-    if (last) break;
-    // the rows of pivot k+1
-    if (!own_k1) {
-      if (tid == 0) wait_flag(pr, pr.flags + (size_t)(k + 1) * Br + p);
-      __syncthreads();
-      const double* vsrc = pr.V + ((size_t)((k + 1) % vslots) * Br + p) * h * E;
-      for (int l = tid; l < h; l += T) sm_store<Ar>(pnxt, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
-    }
+    update_slots<Ar, T>(f, tile, coef, pc, h, hr, sb, nb);
+    __syncthreads();  // the next phase reads these columns (threads update other elements)
+    MGS_TR(kk, 4);
+    return G;
+  };
+
+  // the rows of pivot kk, published by its owner, into pbk(kk)
+  auto receive = [&](int kk) {
+    if (tid == 0) wait_flag(pr, pr.flags + (size_t)kk * Br + p);
     __syncthreads();
+    const double* vsrc = pr.V + ((size_t)(kk % vslots) * Br + p) * h * E;
+    double* dst = pbk(kk);
+    for (int l = tid; l < h; l += T) sm_store<Ar>(dst, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
+    __syncthreads();
+  };
+
+  // ---------------------------------------------------------------- the steps
+  for (int k = 0; k < nc;) {
+    const bool last = (k == nc - 1);
+    const bool own_k = (k % Bc) == c;
+    const bool own_k1 = !last && ((k + 1) % Bc) == c;
+    const bool own_k2 = Bc >= 2 && k + 2 < nc && ((k + 2) % Bc) == c;  // then !own_k1
+    const int s0 = (k + 1 - c + Bc - 1) / Bc;
+    const int first = max(s0, 0);  // first owned slot with a column > k
+    const int nact = w - first;    // owned columns j > k
+    if (nact <= 0 && !(last && own_k)) break;  // nothing left for this cluster
+    MGS_TR(k, 0);
+
+    if (own_k2) {
+      // column k+2 is the next pivot this cluster publishes: pivot k, then pivot k+1 on it
+      // before any bulk work; the bulk of steps k and k+1 follows
+      const real G0 = critical(k, k + 2, false, 0);
+      receive(k + 1);
+      MGS_TR(k, 1);
+      const real G1 = critical(k + 1, k + 2, true, 1);
+      bulk(k, first + 1, true, G0);
+      bulk(k + 1, first + 1, true, G1);
+      MGS_TR(k, 5);
+      k += 2;  // pivot k+2 is this cluster's own, already in pbk(k + 2)
+      continue;
+    }
+
+    real G{};
+    if (own_k1) G = critical(k, k + 1, true, 1);
+    MGS_TR(k, 1);
+    G = bulk(k, own_k1 ? first + 1 : first, own_k1, G);
+    if (last) {
+      // only the owner of the last column is left; for [A b] its norm is z and what is
+      // left of it is the residual b - A x
+      if (p == 0 && tid == 0) {
+        st_real(pr.Gd + (size_t)k * L, G);
+        if (!pr.aug && !Ar::positive(G)) set_status(pr.status, ST_ERANK);
+      }
+      if (pr.aug) {
+        const double* ts = tile + (size_t)(k / Bc) * E * h;
+        for (int l = tid; l < hr; l += T) g_store<Ar>(pr.b + (size_t)(r0 + l) * E, sm_load<Ar>(ts, h, l));
+      }
+      break;
+    }
+    // the rows of pivot k+1
+    if (!own_k1) receive(k + 1);
     MGS_TR(k, 5);
+    ++k;
   }
   // no CTA may go on (and, after an abort, exit) while a peer still reads its shared
   // memory; then the epilogue needs all columns, rows of R and G_kk
