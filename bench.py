@@ -564,7 +564,7 @@ def run_gpu_batched(args, rank, world):
     ops = sum(fp64_ops(L, A.shape[1], A.shape[0]) for A, _ in host)
     # distinct device copies of the batch for warm-up + timed steps (pools are overwritten)
     base = mg.make_batch(host, dev)
-    best, times = tuner.tune_batched(base, reps=1)
+    best, best_order, times = tuner.tune_batched(base, reps=1)
     batches = [mg.Batch(base.A_pool.clone(), base.b_pool.clone(), base.x_pool.clone(), base.a_off, base.b_off,
                         base.x_off, base.m, base.n, base.max_m, base.max_n, base.order) for _ in range(K + W)]
     need = mg._binding.batched_workspace_bytes(L, batch, base.max_m, base.max_n, best)
@@ -653,7 +653,8 @@ def run_gpu_batched(args, rank, world):
         "config": batched_config(args.workload, world),
         "launch": {"max_m": base.max_m, "max_n": base.max_n,
                    "how": "one persistent launch per step, replayed from a CUDA graph",
-                   "tune": {"threads": best[0], "ctas_per_sm": best[1], "candidates_ms": times}},
+                   "tune": {"threads": best[0], "ctas_per_sm": best[1], "split": best[2], "chunks": best[3],
+                            "order": best_order, "candidates_ms": times}},
         "e2e": {"value": world * batch / (e2e_ms / 1000.0), "unit": "systems/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": base.x_pool.numel() * 8},
         "gpu_launches": K,

@@ -91,7 +91,8 @@ size_t mgs_workspace_bytes(int limbs, int m, int n, int with_rhs);
  *   out[4] threads per CTA: 128, or 256 where a CTA owns 16 or more columns (two warps
  *          per SM sub-partition hide each other's FP64 latency in the long loops).
  *   MGS_ROWS = h overrides the rows per row block (default 64); MGS_CTA_THREADS = 128 |
- *   256 the threads per CTA.
+ *   256 the threads per CTA; MGS_CTAS_PER_SM = 1 | 2 how many CTAs of the solve share an
+ *   SM (default 1: each has the SM's FP64 unit to itself; 2 doubles the column groups).
  * Returns MGS_OK, MGS_EINVAL or MGS_ENOSPACE (no layout fits shared memory).
  */
 int mgs_plan_query(int limbs, int m, int n, int with_rhs, int* out);
@@ -169,6 +170,10 @@ typedef struct {
                       keeps 32 rows); the CTAs of a system form a thread-block cluster, each
                       holds a slice of the rows, the slices' Gram partials are summed
                       through distributed shared memory */
+  int chunks;      /* most lanes that share one (column, part) of a system's Gram row in a
+                      step, i.e. rows per lane = ceil(slice rows / chunks): 0 = as many as
+                      the threads allow (fewest rows per lane, deepest reduction trees);
+                      1..threads caps it (more columns per pass, shallower trees) */
 } mgs_tune;
 
 size_t mgs_batched_workspace_bytes(int limbs, int batch, int max_m, int max_n, const mgs_tune* tune);

@@ -7,6 +7,7 @@ this package only builds it, marshals tensors into it, and generates synthetic i
 from ._binding import (  # noqa: F401
     Batch,
     MGSError,
+    batch_order,
     make_batch,
     ls_adjoint_batched,
     ls_solve_batched,

@@ -26,7 +26,8 @@ EXPORTS = ["mgs_version", "mgs_status_string", "mgs_last_cuda_error", "mgs_works
 
 class MgsTune(ctypes.Structure):
     """Launch shape of the batched solve (mgs_tune in the C header)."""
-    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("split", ctypes.c_int)]
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("split", ctypes.c_int),
+                ("chunks", ctypes.c_int)]
 
 _lib = None
 
@@ -296,6 +297,14 @@ class Batch:
         self.batch = int(m.numel())
         self.limbs = int(A_pool.shape[-1])
 
+    def set_order(self, kind):
+        """Set the hand-out order of the work queue (see batch_order); returns self."""
+        import torch
+
+        ords = batch_order(self.m.cpu().numpy(), self.n.cpu().numpy(), kind)
+        self.order = None if ords is None else torch.from_numpy(ords).to(self.A_pool.device)
+        return self
+
     def with_R(self):
         """Allocate the packed-R output pool (n(n+1)/2 elements per system)."""
         import torch
@@ -308,9 +317,32 @@ class Batch:
         return self
 
 
-def make_batch(systems, device, largest_first=True):
+def batch_order(ms, ns, kind):
+    """The order in which the work queue hands the systems out (an int32 permutation, or
+    None for 0, 1, 2, ...).  "largest": decreasing m n^2, which balances the end of the
+    launch; "interleave": the largest and the smallest alternately (largest, smallest,
+    second largest, ...), so the first wave holds about half the bytes of the largest-first
+    one and fits L2 better, and the queue still ends on middle-sized systems."""
+    import numpy as np
+
+    if kind is None or kind == "natural":
+        return None
+    work = np.asarray(ms, dtype=np.float64) * np.asarray(ns, dtype=np.float64) ** 2
+    desc = np.argsort(-work, kind="stable").astype(np.int32)
+    if kind == "largest":
+        return desc
+    if kind == "interleave":
+        out = np.empty_like(desc)
+        out[0::2] = desc[:(len(desc) + 1) // 2]
+        out[1::2] = desc[::-1][:len(desc) // 2]
+        return out
+    raise ValueError("unknown order %r" % (kind,))
+
+
+def make_batch(systems, device, largest_first=True, order=None):
     """Pack a list of (A (n, m, 2, L), b (m, 2, L)) numpy systems into a Batch (copies to
-    the device).  largest_first: hand the systems out in decreasing m n^2 order."""
+    the device).  order: "largest", "interleave" or "natural" (see batch_order); without
+    it, largest_first=True means "largest" and False "natural"."""
     import numpy as np
     import torch
 
@@ -323,12 +355,11 @@ def make_batch(systems, device, largest_first=True):
     A_pool = np.concatenate([A.reshape(-1, 2, L) for A, _ in systems])
     b_pool = np.concatenate([b.reshape(-1, 2, L) for _, b in systems])
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
-    order = None
-    if largest_first:
-        order = t(np.argsort(-(ms.astype(np.float64) * ns.astype(np.float64) ** 2), kind="stable").astype(np.int32))
+    kind = order if order is not None else ("largest" if largest_first else "natural")
+    ords = batch_order(ms, ns, kind)
     x_pool = torch.zeros((int(ns.sum()), 2, L), dtype=torch.float64, device=device)
     return Batch(t(A_pool), t(b_pool), x_pool, t(a_off), t(b_off), t(x_off), t(ms), t(ns),
-                 int(ms.max()), int(ns.max()), order)
+                 int(ms.max()), int(ns.max()), None if ords is None else t(ords))
 
 
 def batched_workspace_bytes(limbs, batch, max_m, max_n, tune=None):
@@ -338,7 +369,8 @@ def batched_workspace_bytes(limbs, batch, max_m, max_n, tune=None):
 
 def ls_solve_batched(bt, workspace=None, status=None, tune=None, stream=None):
     """Solve every system of Batch `bt` in one launch (A -> Q, b -> residual, x filled).
-    tune = (threads, ctas_per_sm) or None.  Returns the per-system status tensor."""
+    tune = (threads, ctas_per_sm[, split[, chunks]]) or None.  Returns the per-system
+    status tensor."""
     import torch
 
     L = bt.limbs

@@ -53,13 +53,14 @@ struct Plan {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Dynamic shared memory that keeps a second CTA off the SM: each CTA of the solve then has
-// the SM's FP64 unit to itself.
-size_t one_cta_per_sm_smem() {
+// Dynamic shared memory that keeps more than `cps` CTAs off an SM (cps = 1: each CTA of the
+// solve has the SM's FP64 unit to itself; cps = 2: two CTAs share it and hide each other's
+// barrier and reduction latency).
+size_t cta_per_sm_smem(int cps) {
   int dev = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
-  return (size_t)per_sm / 2;
+  return (size_t)per_sm / (size_t)(cps + 1);
 }
 
 int device_sms() {
@@ -70,7 +71,7 @@ int device_sms() {
 }
 
 // Rows per CTA about 64; as many column groups as SMs allow; every row block non-empty.
-bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, Plan& pl) {
+bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, int cps, Plan& pl) {
   if ((L != 1 && L != 2 && L != 4) || n < 1 || m < n) return false;
   const int sms = device_sms();
   if (sms <= 0) return false;
@@ -86,12 +87,12 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, Plan& 
   // the SMs a plain grid would use; otherwise, and for quad double (where the FP64
   // throughput decides), the grid-barrier kernel
   int h = h0;
-  const size_t pad = one_cta_per_sm_smem();
+  const size_t pad = cta_per_sm_smem(cps);
   auto padded = [&](size_t v) { return (pad > v && pad <= kMaxSmem) ? pad : v; };
   for (;;) {
     const int Br = (m + h - 1) / h;
     if (Br > kMaxBr || Br > sms) return false;
-    const int Bc_grid = sms / Br < pl.nc ? sms / Br : pl.nc;
+    const int Bc_grid = cps * sms / Br < pl.nc ? cps * sms / Br : pl.nc;
     if (Bc_grid < 1) return false;
     int kind = want < 0 ? (L <= 2 ? 1 : 0) : want, Bc = Bc_grid;
     // 256 threads (two warps per sub-partition) where a CTA owns many columns: their
@@ -167,7 +168,7 @@ bool compute_plan(int L, int m, int n, int aug, int want, int h0, int T0, Plan& 
 // costs far more host time than a launch.
 bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   struct Entry {
-    int dev, L, m, n, aug, want, h, T;
+    int dev, L, m, n, aug, want, h, T, cps;
     Plan pl;
   };
   static std::mutex mu;
@@ -184,21 +185,23 @@ bool make_plan(int L, int m, int n, int aug, Plan& pl) {
   if (h < 8 || h > 1024) h = 64;
   const char* tenv = std::getenv("MGS_CTA_THREADS");  // 128 | 256 (default: by layout)
   const int T = tenv && std::atoi(tenv) == 256 ? 256 : tenv && std::atoi(tenv) == 128 ? 128 : 0;
+  const char* cenv = std::getenv("MGS_CTAS_PER_SM");  // 1 | 2 (default 1)
+  const int cps = cenv && std::atoi(cenv) == 2 ? 2 : 1;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   {
     std::lock_guard<std::mutex> g(mu);
     for (const Entry& e : cache)
       if (e.dev == dev && e.L == L && e.m == m && e.n == n && e.aug == aug && e.want == want && e.h == h &&
-          e.T == T) {
+          e.T == T && e.cps == cps) {
         pl = e.pl;
         return true;
       }
   }
-  if (!compute_plan(L, m, n, aug, want, h, T, pl)) return false;
+  if (!compute_plan(L, m, n, aug, want, h, T, cps, pl)) return false;
   std::lock_guard<std::mutex> g(mu);
   if (cache.size() >= 256) cache.clear();
-  cache.push_back(Entry{dev, L, m, n, aug, want, h, T, pl});
+  cache.push_back(Entry{dev, L, m, n, aug, want, h, T, cps, pl});
   return true;
 }
 

@@ -14,6 +14,7 @@ namespace {
 
 struct BPlan {
   int T, per_sm, grid, S;  // S: CTAs per system (a thread-block cluster when > 1)
+  int cmax;                // lanes per (column, part) cap (0 = none)
   size_t smem, off_scr, total;
   long long per_cta;
 };
@@ -27,6 +28,8 @@ bool make_bplan(int L, int batch, int max_m, int max_n, const mgs_tune* tune, BP
   bp.per_sm = (tune && tune->ctas_per_sm) ? tune->ctas_per_sm : 1;
   if (bp.T != 128 && bp.T != 256) return false;
   if (bp.per_sm < 1 || bp.per_sm > 4) return false;
+  bp.cmax = tune ? tune->chunks : 0;
+  if (bp.cmax < 0 || bp.cmax > bp.T) return false;
   // systems split over S CTAs when the batch is smaller than the GPU (each slice keeps at
   // least 32 rows); automatic unless the tuning asks for a split
   if (tune && tune->split) {
@@ -124,6 +127,7 @@ int run_batched(int L, double* A, double* b, double* x, double* R, const int64_t
   p.ws = reinterpret_cast<double*>(wb + pl.off_scr);
   p.per_cta = pl.per_cta;
   p.status = dev_status;
+  p.cmax = pl.cmax;
   p.one = 1.0;
   p.nzero = -0.0;
   int rc;

@@ -44,6 +44,7 @@ struct BatchParams {
   double* ws;         // per-CTA scratch, per_cta doubles each
   long long per_cta;
   int* status;  // one word per system
+  int cmax;     // most lanes per (column, part) of a Gram row; 0 = no cap
   double one, nzero;
 };
 
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(T) mgs_batched_kernel(BatchParams bp) {
       const int cols = nc - k, pairs = 2 * cols;
       double* pout = pslice + (size_t)(k & 1) * (bp.max_n + 1) * 2 * PACC;
       int C = T / pairs;
+      if (bp.cmax > 0) C = min(C, bp.cmax);
       C = max(1, min(C, max(ml, 1)));
       const int per_round = T / C;
       for (int base = 0; base < pairs; base += per_round) {

@@ -19,12 +19,12 @@ def ragged(orc, L, count, seed, n_lo=1, n_hi=40, extra_hi=8):
     return systems
 
 
-def run(systems, tune=None, largest_first=True):
+def run(systems, tune=None, largest_first=True, order=None):
     import torch
 
     import paper_1210_0800_gb300 as mg
 
-    bt = mg.make_batch(systems, torch.device("cuda:0"), largest_first=largest_first)
+    bt = mg.make_batch(systems, torch.device("cuda:0"), largest_first=largest_first, order=order)
     st = mg.ls_solve_batched(bt, tune=tune)
     torch.cuda.synchronize()
     return bt, st.cpu().numpy()
@@ -55,16 +55,19 @@ def test_batched_vs_oracle(orc, L, count, seed):
 
 
 def test_batched_shapes_and_order_agree(orc):
-    """Every launch shape and both hand-out orders solve the batch to the same tolerance."""
+    """Every launch shape, chunk cap and hand-out order solves the batch to the same
+    tolerance."""
     systems = ragged(orc, 2, 24, 63)
     ref, _ = run(systems, tune=None, largest_first=False)
-    for tune in [(128, 1), (256, 1), (128, 3), (256, 2)]:
-        bt, st = run(systems, tune=tune, largest_first=True)
+    for tune, order in [((128, 1), "largest"), ((256, 1), "largest"), ((128, 3), "largest"), ((256, 2), "largest"),
+                        ((256, 1, 0, 4), "largest"), ((128, 2, 0, 8), "interleave"), ((256, 1, 2, 16), "interleave"),
+                        ((256, 1, 1, 1), "natural")]:
+        bt, st = run(systems, tune=tune, order=order)
         assert (st == 0).all()
         for i in range(len(systems)):
             x0 = unpack(ref, i, systems)[2]
             x1 = unpack(bt, i, systems)[2]
-            assert rel(orc, x1, x0) <= 1e-26, (tune, i)
+            assert rel(orc, x1, x0) <= 1e-26, (tune, order, i)
 
 
 def test_batched_statuses(orc):
@@ -87,19 +90,31 @@ def test_batched_statuses(orc):
         assert rel(orc, unpack(bt, i, systems)[2], o["x"]) <= TOL[2]
 
 
-def test_autotuner_picks_a_candidate(tmp_path):
+def test_autotuner_searches_and_agrees_with_oracle(orc, tmp_path):
+    """The tuner times shapes, splits, chunk caps and hand-out orders, caches its choice per
+    shape bucket, and the tuned launch agrees with the oracle on a sample of the batch."""
     import torch
 
-    import oracle
     import paper_1210_0800_gb300 as mg
     from paper_1210_0800_gb300 import tune
 
-    systems = ragged(oracle.get(), 2, 32, 65, 8, 24)
+    systems = ragged(orc, 2, 40, 65, 8, 40)
     bt = mg.make_batch(systems, torch.device("cuda:0"))
-    best, times = tune.tune_batched(bt, reps=1, cache_path=str(tmp_path / "c.json"))
-    assert tuple(best) in tune.CANDIDATES and len(times) == len(tune.CANDIDATES)
-    again, _ = tune.tune_batched(bt, cache_path=str(tmp_path / "c.json"))
-    assert tuple(again) == tuple(best)
+    best, order, times = tune.tune_batched(bt, reps=1, cache_path=str(tmp_path / "c.json"))
+    assert order in tune.ORDERS
+    labels = set(times)
+    assert any(lb.split(",")[4] == "interleave" for lb in labels)
+    assert {int(lb.split(",")[2]) for lb in labels} >= set(tune.SPLITS)
+    assert {int(lb.split(",")[3]) for lb in labels} >= {c for c in tune.CHUNKS if c <= best[0]}
+    assert tune._label(tuple(best), order) in times
+    again, order2, _ = tune.tune_batched(bt, cache_path=str(tmp_path / "c.json"))
+    assert tuple(again) == tuple(best) and order2 == order
+    bt2, st = run(systems, tune=tuple(best), order=order)
+    assert (st == 0).all()
+    for i in range(0, len(systems), 5):
+        A, b = systems[i]
+        x = unpack(bt2, i, systems)[2]
+        assert rel(orc, x, orc.ls_solve(A.copy(), b.copy())["x"]) <= TOL[2], i
 
 
 @pytest.mark.parametrize("L,split", [(2, 2), (2, 4), (4, 2), (1, 4)])
