@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
   // block's flag, and G_kk is recorded.  Returns G_kk.  `ab` selects the A-partials buffer
   // (the pre-phase and the phase that follows it use different ones).
   auto critical = [&](int kk, int j, bool publish, int ab) -> real {
+    MGS_TR(kk, 1);
     const double* pc = pbk(kk);
     const int sj = (j - c) / Bc;
     double* pa = pabuf + (size_t)ab * 2 * 2 * PACC;
@@ -337,12 +338,14 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     } else {
       __syncthreads();
     }
+    MGS_TR(kk, 5);
     return G;
   };
 
   // Bulk phase of step kk on the owned slots [sb, w): partials (with G_kk's unless
   // `haveG`), cluster reduction, coefficients, R/y stores, updates.  Returns G_kk.
   auto bulk = [&](int kk, int sb, bool haveG, real G) -> real {
+    MGS_TR(kk, 0);
     const double* pc = pbk(kk);
     const bool norm_here = !haveG;
     const int nb = w - sb;
@@ -409,6 +412,7 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     double* dst = pbk(kk);
     for (int l = tid; l < h; l += T) sm_store<Ar>(dst, h, l, g_load_cg<Ar>(vsrc + (size_t)l * E));
     __syncthreads();
+    MGS_TR(kk, 7);  // kk >= 1: slot 7 of step 0 holds the SM id
   };
 
   // ---------------------------------------------------------------- the steps
@@ -421,25 +425,21 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     const int first = max(s0, 0);  // first owned slot with a column > k
     const int nact = w - first;    // owned columns j > k
     if (nact <= 0 && !(last && own_k)) break;  // nothing left for this cluster
-    MGS_TR(k, 0);
 
     if (own_k2) {
       // column k+2 is the next pivot this cluster publishes: pivot k, then pivot k+1 on it
       // before any bulk work; the bulk of steps k and k+1 follows
       const real G0 = critical(k, k + 2, false, 0);
       receive(k + 1);
-      MGS_TR(k, 1);
       const real G1 = critical(k + 1, k + 2, true, 1);
       bulk(k, first + 1, true, G0);
       bulk(k + 1, first + 1, true, G1);
-      MGS_TR(k, 5);
       k += 2;  // pivot k+2 is this cluster's own, already in pbk(k + 2)
       continue;
     }
 
     real G{};
     if (own_k1) G = critical(k, k + 1, true, 1);
-    MGS_TR(k, 1);
     G = bulk(k, own_k1 ? first + 1 : first, own_k1, G);
     if (last) {
       // only the owner of the last column is left; for [A b] its norm is z and what is
@@ -456,7 +456,6 @@ __global__ void __launch_bounds__(T, 1) mgs_cluster_kernel(Params pr) {
     }
     // the rows of pivot k+1
     if (!own_k1) receive(k + 1);
-    MGS_TR(k, 5);
     ++k;
   }
   // no CTA may go on (and, after an abort, exit) while a peer still reads its shared

@@ -10,8 +10,11 @@ library (lib/trace/), runs a few solves of one size and prints where the time go
 Phases of the grid-barrier kernel, per step k: reduction of the Br partial Gram rows,
 coefficient division, look-ahead update of column k+1, update of the other columns,
 wait for and copy of pivot k+1, partials of step k+1, grid barrier.  Of the cluster
-schedule: phase A (column k+1 on its owner), partials of the other columns, cluster
-barrier and reduction, coefficient division, R/y stores and updates, wait for pivot k+1.
+schedule: the critical phases (a pivot applied to the next column a cluster publishes:
+on the owner of column k+1, and ahead of it on the owner of column k+2), then per bulk
+phase its Gram partials, cluster barrier and reduction, coefficient division, R/y stores
+and updates, and the wait for and copy of the next pivot.  Each phase is the per-step mean
+over the CTAs that ran it, summed over the steps.
 """
 
 from __future__ import annotations
@@ -24,7 +27,7 @@ import numpy as np
 from . import _binding, build, inputs
 
 GRID_PHASES = ["reduce", "coef", "lookahead", "update", "wait+copy", "partials", "barrier"]
-CLUSTER_PHASES = ["A (column k+1)", "partials", "sync+reduce", "coef", "store+update", "wait pivot"]
+CLUSTER_PHASES = ["critical phases", "bulk partials", "barrier+reduce", "coef", "store+update", "pivot wait+copy"]
 
 
 def _load_trace_library():
@@ -70,24 +73,41 @@ def summarize(plan, tr) -> str:
     grid = plan["kernel"] == "grid"
     names = GRID_PHASES if grid else CLUSTER_PHASES
     tot = np.zeros(len(names))
-    for k in range(nc - 1):
+    for k in range(nc - 1 if grid else nc):
         row = tr[k]
         act = row[:, 0] > 0
-        if not act.any():
-            continue
         if grid:
+            if not act.any():
+                continue
             for i in range(len(names)):
                 end = tr[k + 1, act, 0] if i == len(names) - 1 else row[act, i + 1]
                 tot[i] += np.mean(end - row[act, i])
         else:
-            # stamps 0 start, 1 after A, 6 after the partials (0 where the step had none),
-            # 2 after the cluster reduction, 3 coefficients, 4 updates, 5 pivot received
-            has = row[act, 6] > 0
-            mid = np.where(has, row[act, 6], row[act, 1])
-            b = [row[act, 0], row[act, 1], mid, row[act, 2], row[act, 3], row[act, 4], row[act, 5]]
-            for i in range(len(names)):
-                tot[i] += np.mean(b[i + 1] - b[i])
-    t0 = tr[0, :, 0][tr[0, :, 0] > 0].min()
+            # stamps of step k: 1/5 start/end of a critical phase with pivot k; 0 bulk start,
+            # 6 after its partials (0 where it had none), 2 after the cluster reduction,
+            # 3 after the coefficients, 4 bulk end; 7 (k >= 1) pivot k received
+            cr = (row[:, 1] > 0) & (row[:, 5] > 0)
+            if cr.any():
+                tot[0] += np.mean(row[cr, 5] - row[cr, 1])
+            bk = (row[:, 0] > 0) & (row[:, 4] > 0)
+            if bk.any():
+                r = row[bk]
+                mid = np.where(r[:, 6] > 0, r[:, 6], r[:, 0])
+                tot[1] += np.mean(mid - r[:, 0])
+                tot[2] += np.mean(r[:, 2] - mid)
+                tot[3] += np.mean(r[:, 3] - r[:, 2])
+                tot[4] += np.mean(r[:, 4] - r[:, 3])
+            if k >= 1:
+                prev = tr[k - 1]
+                waits = []
+                for c in np.nonzero(row[:, 7] > 0)[0]:
+                    before = [v for v in (prev[c, 4], prev[c, 5]) if 0 < v < row[c, 7]]
+                    if before:
+                        waits.append(row[c, 7] - max(before))
+                if waits:
+                    tot[5] += float(np.mean(waits))
+    first = tr[0, :, :7]
+    t0 = first[first > 0].min()
     ep = tr[nc]
     lines.append("sweep %.1f us, solve %.1f us" % ((ep[:, 0].max() - t0) / 1e3, (ep[:, 3].max() - t0) / 1e3))
     for nm, v in zip(names, tot):

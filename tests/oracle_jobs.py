@@ -72,6 +72,9 @@ class Jobs:
     """Handles of the submitted jobs: get(name) waits for one result."""
 
     def __init__(self, names):
+        import oracle
+
+        oracle.get()  # build the oracle here if it is missing or stale, not in every worker
         ctx = mp.get_context("spawn")
         procs = max(1, min(len(names), (os.cpu_count() or 2) - 2))
         self.pool = ctx.Pool(procs)
