@@ -410,6 +410,9 @@ def run_reference(args, config, unit, rank, world):
         "config": config,
         "cpu_baseline": {"value": value, "unit": unit, "cores": procs, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "reference_step": res[0][2] + (" (one system of each GPU step's batch)" if args.workload in BATCHED or
+                                       args.workload in DIFF else
+                                       " (one Newton step of a GPU run)" if args.workload in NEWTON else ""),
         "single_core_s_per_step": statistics.median(secs),
         "nproc": cores,
         "wall_s": wall,
