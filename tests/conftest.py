@@ -22,6 +22,8 @@ def pytest_collection_modifyitems(session, config, items):
     any test runs, so before the first GPU call): they run in spawned worker processes
     while the other tests use the GPU."""
     global _JOBS
+    if config.option.collectonly:
+        return
     names = []
     for it in items:
         for mk in it.iter_markers("oracle_jobs"):

@@ -21,6 +21,7 @@ FULLSIZE = {
     "dd_256": (2, 256, 256, ("plain", 7702256), False, 2),
     "dd_512": (2, 512, 512, ("plain", 7702512), False, 2),
     "qd_512": (4, 512, 512, ("plain", 7704512), False, 4),
+    "d_256": (1, 256, 256, ("plain", 7701256), False, 1),
     # the extreme-value DD workload: the DD oracle, the truth (the same stored numbers
     # solved at twice the limbs) and the complex-double solve of the leading limbs
     "c2_dd": (2, 256, 256, ("workload", "c2", 0), True, 2),

@@ -50,12 +50,13 @@ def test_c0_dd_32x32_vs_oracle(orc):
     compare_ls(orc, A, b)
 
 
-@pytest.mark.oracle_jobs("c1_qd_320x256", "dd_256", "dd_512", "qd_512")
-@pytest.mark.parametrize("name", ["c1_qd_320x256", "dd_256", "dd_512", "qd_512"])
+@pytest.mark.parametrize("name", [pytest.param(nm, marks=pytest.mark.oracle_jobs(nm)) for nm in
+                                  ("c1_qd_320x256", "dd_256", "dd_512", "qd_512", "d_256")])
 def test_fullsize_vs_oracle(orc, jobs, name):
     """The headline quad-double m = 320, n = 256 system (the benchmark's first timed
-    system) and the m = n = 256 and 512 sweep points in DD and QD (where the plan picks
-    256 threads per CTA), in the default plan, at 1e-26 (DD) / 1e-56 (QD)."""
+    system), the m = n = 256 and 512 sweep points in DD and QD (where the plan picks 256
+    threads per CTA) and complex double at m = n = 256, in the default plan, at 1e-26 (DD),
+    1e-56 (QD), 1e-10 (complex double)."""
     import oracle_jobs
 
     A, b = oracle_jobs.inputs_of(name)
@@ -104,9 +105,8 @@ def test_c2_dd_256_extreme_vs_truth(orc, jobs):
     _judge_extreme(orc, g, ref, truth, low, 2.0 ** -104, 10, 1e-8, "c2 DD 256x256 extreme")
 
 
-@pytest.mark.oracle_jobs(*["qdx_%dx%d_L%d" % (m, n, lo) for m, n in ((64, 64), (90, 65), (160, 130))
-                           for lo in (4, 8, 2)])
-@pytest.mark.parametrize("m,n", [(64, 64), (90, 65), (160, 130)])
+@pytest.mark.parametrize("m,n", [pytest.param(m, n, marks=pytest.mark.oracle_jobs(
+    *["qdx_%dx%d_L%d" % (m, n, lo) for lo in (4, 8, 2)])) for m, n in ((64, 64), (90, 65), (160, 130))])
 def test_qd_extreme_vs_truth(orc, jobs, m, n):
     """The extreme scaling of the DD workload in quad double, through the QD kernel's
     paired back substitution (n = 65: a block with an odd row count): the GPU against the
