@@ -53,7 +53,8 @@ extern "C" {
 #define MGS_ECUDA 5      /* host: a CUDA call failed; mgs_last_cuda_error() returns its cudaError_t */
 #define MGS_ENOSPACE 6   /* host: workspace too small, or the problem exceeds what one GPU solve holds */
 
-/* Library version (major * 10000 + minor * 100 + patch). */
+/* Library version (major * 10000 + minor * 100 + patch).  0.2.0 (200): mgs_tune gained the
+ * `chunks` field; callers built against 0.1 must be rebuilt. */
 int mgs_version(void);
 
 /* Human-readable name of a status code. */

@@ -293,7 +293,7 @@ int ls_solve_gated(int L, double* A, int lda, double* b, double* x, double* z, i
 
 extern "C" {
 
-int mgs_version(void) { return 100; }
+int mgs_version(void) { return 200; }
 
 const char* mgs_status_string(int code) {
   switch (code) {

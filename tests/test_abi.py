@@ -102,3 +102,13 @@ def test_host_argument_checks_wait_probe(lib):
     assert L.mgs_wait_probe(good, 2, 1000, st) == 1          # unknown kind
     assert L.mgs_wait_probe(good, 1, 0, st) == 1             # no time limit
     assert L.mgs_wait_probe(good, 0, 20 * 10 ** 9, st) == 1  # above 10 s
+
+
+def test_version_and_tune_struct(lib):
+    """The version announces the mgs_tune layout the binding marshals (four ints)."""
+    from paper_1210_0800_gb300 import _binding
+
+    lib.mgs_version.restype = ctypes.c_int
+    assert lib.mgs_version() == 200
+    assert ctypes.sizeof(_binding.MgsTune) == 4 * ctypes.sizeof(ctypes.c_int)
+    assert [f[0] for f in _binding.MgsTune._fields_] == ["threads", "ctas_per_sm", "split", "chunks"]
